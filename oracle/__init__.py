@@ -1,0 +1,7 @@
+"""FP64 CPU oracle for the SWiFT-IR block-matching step.
+
+Test infrastructure only: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the library.
+"""
+from .swim import *  # noqa: F401,F403
+from . import swim  # noqa: F401
