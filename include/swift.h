@@ -1,0 +1,170 @@
+/*
+ * swift.h -- C ABI of the GB300 (sm_103a) SWiFT-IR block-matching library.
+ *
+ * The library computes the "swim" matching step of SWiFT-IR (Wetzel et al.,
+ * Sec. III): for each pair of apodised match windows, the forward 2D
+ * transforms of both windows, their frequency-domain product with its
+ * amplitudes rescaled by a power-law whitening exponent (phases untouched),
+ * the inverse transform (the pixel-level match response of Fig. 2), the peak
+ * of that response (the relative shift), the peak's signal-to-noise ratio as a
+ * Z score against the background, and a subpixel peak position.
+ *
+ * Every step runs in this library's own CUDA kernels; there is no CPU path.
+ *
+ * Conventions shared by every entry point
+ *   - All image, origin, level, affine and result arrays are DEVICE pointers
+ *     owned by the caller.  A plan owns only its own small tables.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and do not synchronise the host.
+ *   - Argument errors are detected on the host before any launch and return a
+ *     status other than SWIFT_OK with nothing written.  Launch failures return
+ *     SWIFT_ERR_CUDA.  Per-window data problems are reported in
+ *     swift_result.status, never as a call error.
+ *   - A plan may be used by one stream at a time.  No entry point throws.
+ */
+#ifndef SWIFT_H_
+#define SWIFT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SWIFT_OK = 0,
+  SWIFT_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is invalid      */
+  SWIFT_ERR_UNSUPPORTED = 2, /* valid, but not built (e.g. a window size)    */
+  SWIFT_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed         */
+  SWIFT_ERR_OOM = 4,         /* a plan table could not be allocated          */
+  SWIFT_ERR_TIMEOUT = 5      /* a device-side bounded wait gave up           */
+} swift_status;
+
+/* Apodisation: the paper's cosine taper (Sec. III, "apodization").  HANN is
+ * the periodic Hann window, a[k] = (1 - cos(2 pi k / n)) / 2, and equals
+ * TUKEY with alpha = 1; TUKEY(alpha) is flat in the middle with raised-cosine
+ * ramps of alpha*n/2 samples at each edge.  The 2D taper is a[y] a[x]. */
+typedef enum { SWIFT_APOD_NONE = 0, SWIFT_APOD_HANN = 1, SWIFT_APOD_TUKEY = 2 } swift_apod;
+
+/* Element type of the input images. */
+typedef enum { SWIFT_IN_U8 = 0, SWIFT_IN_F32 = 1 } swift_dtype;
+
+/* Arithmetic of the transforms.  FP32 is the plain form. */
+typedef enum { SWIFT_PREC_FP32 = 0, SWIFT_PREC_BF16X2 = 1, SWIFT_PREC_FP16X2 = 2 } swift_precision;
+
+/* Per-window status codes (swift_result.status). */
+enum {
+  SWIFT_WIN_OK = 0,
+  SWIFT_WIN_OUT_OF_BOUNDS = 1, /* a window leaves its image                     */
+  SWIFT_WIN_FLAT = 2,          /* all pixels of either window are equal         */
+  SWIFT_WIN_NONFINITE = 3      /* a NaN or infinity in either (float) window    */
+};
+
+/* One matching configuration (one pyramid level), Sec. III:
+ *   n                    window side; 64, 128 or 256 (power of two)
+ *   whiten_exponent      w in [0, 1]: magnitudes of the cross-power spectrum
+ *                        C = M conj(R) are raised to 1 - w (G = C |C|^-w);
+ *                        0 = plain correlation, 1 = phase-only correlation
+ *   apod, tukey_alpha    taper (alpha in (0, 1], used by TUKEY only)
+ *   snr_exclusion_radius pixels within this wrapped Euclidean distance of the
+ *                        peak are left out of the SNR background (>= 0)      */
+typedef struct {
+  int32_t n;
+  float whiten_exponent;
+  int32_t apod;
+  float tukey_alpha;
+  float snr_exclusion_radius;
+} swift_level;
+
+/* An image (section) or a stack of patches, row-major, on the device.
+ *   data    device pointer to uint8 or float32 elements (the plan's dtype)
+ *   pitch   elements between consecutive rows
+ *   stride  elements between consecutive images of a stack: the K sections
+ *           averaged into a reference model (Sec. III, "remod"), or the
+ *           patches of patch mode
+ *   height, width  image size in pixels (ignored in patch mode)
+ *   count   number of sections averaged into each window (>= 1); the window
+ *           is then their mean.  Use 1 for the moving image.                 */
+typedef struct {
+  const void* data;
+  int64_t pitch;
+  int64_t stride;
+  int32_t height;
+  int32_t width;
+  int32_t count;
+} swift_image;
+
+/* A batch of window pairs.
+ *   ref, mov     HOST arrays of n_levels images: level l's windows are cut
+ *                from ref[l] (reference, possibly a K-section model) and
+ *                mov[l] (moving)
+ *   ref_origin   device int32 [B][2] (y, x) window origins in ref; NULL in
+ *                patch mode
+ *   mov_origin   device int32 [B][2] origins in mov; NULL in patch mode
+ *   level        device int32 [B] level of each window; NULL = all level 0
+ *   n_windows    B >= 0 (0 is a no-op)
+ *   patch_mode   0: windows are cut from images at the origins;
+ *                1: window b of level l is the n x n patch starting at
+ *                   data + b * stride (pitch = n) of ref[l] / mov[l]         */
+typedef struct {
+  const swift_image* ref;
+  const swift_image* mov;
+  const int32_t* ref_origin;
+  const int32_t* mov_origin;
+  const int32_t* level;
+  int64_t n_windows;
+  int32_t patch_mode;
+} swift_batch;
+
+/* Result of one window pair (32 bytes).
+ *   dy, dx   integer peak of the match response as a signed shift in
+ *            [-n/2, n/2): the moving window's content sits at
+ *            reference + (dy, dx).  Ties go to the smallest row-major index.
+ *   sy, sx   subpixel shift: integer peak plus a separable three-point
+ *            parabola offset in [-1/2, 1/2] per axis (0 if not concave)
+ *   snr      (peak - mean_bg) / std_bg over background pixels farther than
+ *            the exclusion radius from the peak (population std);
+ *            +inf if std_bg = 0 and the peak is above the mean
+ *   peak     match response at the peak; the response is
+ *            Re(IDFT(G)) / n^2, so an exact shift under phase-only matching
+ *            gives 1 - 1/n^2
+ *   status   SWIFT_WIN_* ; outputs are 0 unless status is SWIFT_WIN_OK      */
+typedef struct {
+  int32_t dy, dx;
+  float sy, sx;
+  float snr;
+  float peak;
+  int32_t status;
+  int32_t reserved;
+} swift_result;
+
+typedef struct swift_plan_s* swift_plan;
+
+/* Create a plan for up to n_levels (1..8) matching levels.  Builds the taper
+ * and twiddle tables (FP64 on the host, stored as FP32 on the current device).
+ * max_windows bounds n_windows of later calls (> 0).  Returns
+ * SWIFT_ERR_UNSUPPORTED for a window size or precision this build lacks.
+ * On success *out receives the plan; on failure *out is set to NULL. */
+swift_status swift_plan_create(const swift_level* levels, int32_t n_levels, swift_dtype in,
+                               swift_precision prec, int64_t max_windows, swift_plan* out);
+
+/* Release a plan's tables (NULL is a no-op).  The caller must make sure no
+ * launch that uses the plan is still running. */
+swift_status swift_plan_destroy(swift_plan plan);
+
+/* Forward match of a batch (Sec. III, the swim step): one result per window
+ * written to out (device, [n_windows]).  Stream-ordered, no host sync. */
+swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_result* out,
+                               void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* swift_status_string(swift_status s);
+
+/* Library version string, e.g. "swift-gb300 0.1 sm_103a". */
+const char* swift_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWIFT_H_ */

@@ -1,0 +1,93 @@
+"""ctypes view of the C ABI declared in ``include/swift.h``.
+
+Loads the in-tree ``libswift_gb300.so``.  There is no fallback: if the library
+is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswift_gb300.so")
+
+# status codes
+SWIFT_OK = 0
+SWIFT_ERR_INVALID_ARG = 1
+SWIFT_ERR_UNSUPPORTED = 2
+SWIFT_ERR_CUDA = 3
+SWIFT_ERR_OOM = 4
+SWIFT_ERR_TIMEOUT = 5
+
+APOD = {"none": 0, "hann": 1, "tukey": 2}
+DTYPE = {"u8": 0, "f32": 1}
+PRECISION = {"fp32": 0, "bf16x2": 1, "fp16x2": 2}
+
+WIN_OK, WIN_OUT_OF_BOUNDS, WIN_FLAT, WIN_NONFINITE = 0, 1, 2, 3
+
+# every symbol include/swift.h declares
+EXPORTS = (
+    "swift_plan_create",
+    "swift_plan_destroy",
+    "swift_match_batch",
+    "swift_status_string",
+    "swift_version",
+)
+
+
+class SwiftLevel(C.Structure):
+    _fields_ = [("n", C.c_int32), ("whiten_exponent", C.c_float), ("apod", C.c_int32),
+                ("tukey_alpha", C.c_float), ("snr_exclusion_radius", C.c_float)]
+
+
+class SwiftImage(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("pitch", C.c_int64), ("stride", C.c_int64),
+                ("height", C.c_int32), ("width", C.c_int32), ("count", C.c_int32)]
+
+
+class SwiftBatch(C.Structure):
+    _fields_ = [("ref", C.POINTER(SwiftImage)), ("mov", C.POINTER(SwiftImage)),
+                ("ref_origin", C.c_void_p), ("mov_origin", C.c_void_p), ("level", C.c_void_p),
+                ("n_windows", C.c_int64), ("patch_mode", C.c_int32)]
+
+
+class SwiftResult(C.Structure):
+    _fields_ = [("dy", C.c_int32), ("dx", C.c_int32), ("sy", C.c_float), ("sx", C.c_float),
+                ("snr", C.c_float), ("peak", C.c_float), ("status", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+assert C.sizeof(SwiftResult) == 32
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    lib.swift_plan_create.argtypes = [C.POINTER(SwiftLevel), C.c_int32, C.c_int, C.c_int, C.c_int64,
+                                      C.POINTER(C.c_void_p)]
+    lib.swift_plan_create.restype = C.c_int
+    lib.swift_plan_destroy.argtypes = [C.c_void_p]
+    lib.swift_plan_destroy.restype = C.c_int
+    lib.swift_match_batch.argtypes = [C.c_void_p, C.POINTER(SwiftBatch), C.c_void_p, C.c_void_p]
+    lib.swift_match_batch.restype = C.c_int
+    lib.swift_status_string.argtypes = [C.c_int]
+    lib.swift_status_string.restype = C.c_char_p
+    lib.swift_version.argtypes = []
+    lib.swift_version.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+class SwiftError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {lib.swift_status_string(code).decode()}")
+
+
+def check(code: int, where: str):
+    if code != SWIFT_OK:
+        raise SwiftError(code, where)

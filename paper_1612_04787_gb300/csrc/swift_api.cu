@@ -1,0 +1,225 @@
+// Host side of the C ABI: plans (taper and twiddle tables), argument checks,
+// dispatch to the per-size kernels.  No exceptions cross this boundary.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <new>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/swift.h"
+#include "swift_internal.h"
+
+namespace {
+
+constexpr int kMaxLevels = 8;
+constexpr int kSizes[3] = {64, 128, 256};
+
+int size_slot(int n) {
+  for (int i = 0; i < 3; ++i)
+    if (kSizes[i] == n) return i;
+  return -1;
+}
+
+// 1D taper in FP64 (Sec. III: cosine taper).  Periodic convention: Hann is
+// a[k] = (1 - cos(2 pi k / n)) / 2; Tukey(alpha) has raised-cosine ramps of
+// alpha*n/2 samples at each edge and is 1 in between.
+void taper_table(int n, int apod, double alpha, double* a) {
+  if (apod == SWIFT_APOD_NONE) {
+    for (int k = 0; k < n; ++k) a[k] = 1.0;
+    return;
+  }
+  if (apod == SWIFT_APOD_HANN) alpha = 1.0;
+  const double ramp = alpha * n / 2.0;
+  for (int k = 0; k < n; ++k) {
+    double v = 1.0;
+    if (k < ramp)
+      v = 0.5 * (1.0 - cos(M_PI * k / ramp));
+    else if (k > n - ramp)
+      v = 0.5 * (1.0 - cos(M_PI * (n - k) / ramp));
+    a[k] = v;
+  }
+}
+
+}  // namespace
+
+struct swift_plan_s {
+  int n_levels = 0;
+  swift_level levels[kMaxLevels];
+  swift_dtype dtype = SWIFT_IN_U8;
+  swift_precision prec = SWIFT_PREC_FP32;
+  int64_t max_windows = 0;
+  int device = 0;
+  float* taper[kMaxLevels] = {};
+  double inv_sum_a[kMaxLevels] = {};
+  float2* twiddle[3] = {};
+};
+
+static swift_status release(swift_plan p) {
+  if (!p) return SWIFT_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) cudaSetDevice(p->device);
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (p->taper[l]) cudaFree(p->taper[l]);
+  for (int i = 0; i < 3; ++i)
+    if (p->twiddle[i]) cudaFree(p->twiddle[i]);
+  if (cur != p->device) cudaSetDevice(cur);
+  delete p;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_levels, swift_dtype in,
+                                          swift_precision prec, int64_t max_windows, swift_plan* out) {
+  if (out) *out = nullptr;
+  if (!out || !levels || n_levels < 1 || n_levels > kMaxLevels || max_windows <= 0) return SWIFT_ERR_INVALID_ARG;
+  if (in != SWIFT_IN_U8 && in != SWIFT_IN_F32) return SWIFT_ERR_INVALID_ARG;
+  if (prec != SWIFT_PREC_FP32 && prec != SWIFT_PREC_BF16X2 && prec != SWIFT_PREC_FP16X2) return SWIFT_ERR_INVALID_ARG;
+  if (prec != SWIFT_PREC_FP32) return SWIFT_ERR_UNSUPPORTED;
+  for (int l = 0; l < n_levels; ++l) {
+    const swift_level& lv = levels[l];
+    if (lv.n < 2 || (lv.n & (lv.n - 1)) != 0) return SWIFT_ERR_INVALID_ARG;
+    if (!(lv.whiten_exponent >= 0.f && lv.whiten_exponent <= 1.f)) return SWIFT_ERR_INVALID_ARG;
+    if (lv.apod != SWIFT_APOD_NONE && lv.apod != SWIFT_APOD_HANN && lv.apod != SWIFT_APOD_TUKEY)
+      return SWIFT_ERR_INVALID_ARG;
+    if (lv.apod == SWIFT_APOD_TUKEY && !(lv.tukey_alpha > 0.f && lv.tukey_alpha <= 1.f)) return SWIFT_ERR_INVALID_ARG;
+    if (!(lv.snr_exclusion_radius >= 0.f) || !(lv.snr_exclusion_radius < 1e4f)) return SWIFT_ERR_INVALID_ARG;
+    if (size_slot(lv.n) < 0) return SWIFT_ERR_UNSUPPORTED;
+  }
+  swift_plan p = new (std::nothrow) swift_plan_s();
+  if (!p) return SWIFT_ERR_OOM;
+  p->n_levels = n_levels;
+  memcpy(p->levels, levels, sizeof(swift_level) * n_levels);
+  p->dtype = in;
+  p->prec = prec;
+  p->max_windows = max_windows;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return SWIFT_ERR_CUDA;
+  }
+  double a[256];
+  float af[256];
+  for (int l = 0; l < n_levels; ++l) {
+    const int n = levels[l].n;
+    taper_table(n, levels[l].apod, levels[l].tukey_alpha, a);
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) {
+      s += a[k];
+      af[k] = static_cast<float>(a[k]);
+    }
+    p->inv_sum_a[l] = 1.0 / (s * s);
+    if (cudaMalloc(&p->taper[l], sizeof(float) * n) != cudaSuccess ||
+        cudaMemcpy(p->taper[l], af, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+      release(p);
+      cudaGetLastError();
+      return SWIFT_ERR_OOM;
+    }
+    // twiddle table W_n^{j m} = exp(-2 pi i j m / n), j < R1, m < R2, stored [m][j]
+    const int slot = size_slot(n);
+    if (!p->twiddle[slot]) {
+      int r1 = 0, r2 = 0;
+      swift::forward_radices(n, &r1, &r2);
+      float2 tw[256];
+      for (int m = 0; m < r2; ++m)
+        for (int j = 0; j < r1; ++j) {
+          const int e = (j * m) % n;
+          const double ang = -2.0 * M_PI * e / n;
+          tw[m * r1 + j] = make_float2(static_cast<float>(cos(ang)), static_cast<float>(sin(ang)));
+        }
+      if (cudaMalloc(&p->twiddle[slot], sizeof(float2) * n) != cudaSuccess ||
+          cudaMemcpy(p->twiddle[slot], tw, sizeof(float2) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+        release(p);
+        cudaGetLastError();
+        return SWIFT_ERR_OOM;
+      }
+    }
+  }
+  *out = p;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_destroy(swift_plan plan) { return release(plan); }
+
+static bool image_ok(const swift_image& im, int n, int patch_mode, int64_t B) {
+  if (!im.data || im.count < 1) return false;
+  if (patch_mode) {
+    if (im.stride < static_cast<int64_t>(n) * n && B > 1) return false;
+    return im.count == 1;
+  }
+  if (im.height < 1 || im.width < 1 || im.pitch < im.width) return false;
+  if (im.count > 1 && im.stride < im.pitch * im.height) return false;
+  return true;
+}
+
+extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_result* out,
+                                          void* stream) {
+  if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
+  const int64_t B = batch->n_windows;
+  if (B < 0 || B > plan->max_windows) return SWIFT_ERR_INVALID_ARG;
+  if (B == 0) return SWIFT_OK;
+  if (!out || !batch->ref || !batch->mov) return SWIFT_ERR_INVALID_ARG;
+  if (B * 4 > static_cast<int64_t>(0x7fffffff)) return SWIFT_ERR_INVALID_ARG;  // grid limit
+  const int pm = batch->patch_mode ? 1 : 0;
+  if (!pm && (!batch->ref_origin || !batch->mov_origin)) return SWIFT_ERR_INVALID_ARG;
+  const int used_levels = batch->level ? plan->n_levels : 1;
+  for (int l = 0; l < used_levels; ++l) {
+    const int n = plan->levels[l].n;
+    if (!image_ok(batch->ref[l], n, pm, B) || !image_ok(batch->mov[l], n, pm, B)) return SWIFT_ERR_INVALID_ARG;
+    if (batch->mov[l].count != 1) return SWIFT_ERR_INVALID_ARG;
+  }
+  // report (and clear) an asynchronous failure left by earlier work
+  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int l = 0; l < used_levels; ++l) {
+    const swift_level& lv = plan->levels[l];
+    const swift_image& ri = batch->ref[l];
+    const swift_image& mi = batch->mov[l];
+    swift::MatchLaunch L;
+    L.ref = ri.data;
+    L.mov = mi.data;
+    L.ref_pitch = pm ? lv.n : ri.pitch;
+    L.mov_pitch = pm ? lv.n : mi.pitch;
+    L.ref_stride = pm ? (ri.stride ? ri.stride : static_cast<long long>(lv.n) * lv.n) : ri.stride;
+    L.mov_stride = pm ? (mi.stride ? mi.stride : static_cast<long long>(lv.n) * lv.n) : mi.stride;
+    L.ref_h = ri.height;
+    L.ref_w = ri.width;
+    L.mov_h = mi.height;
+    L.mov_w = mi.width;
+    L.ref_count = ri.count;
+    L.patch_mode = pm;
+    L.ref_origin = batch->ref_origin;
+    L.mov_origin = batch->mov_origin;
+    L.level_idx = batch->level;
+    L.level = l;
+    L.n_windows = B;
+    L.w = lv.whiten_exponent;
+    const double r2 = static_cast<double>(lv.snr_exclusion_radius) * lv.snr_exclusion_radius;
+    L.radius2 = static_cast<float>(floor(r2));
+    L.inv_sum_a = plan->inv_sum_a[l];
+    L.taper = plan->taper[l];
+    L.twiddle = plan->twiddle[size_slot(lv.n)];
+    L.out = out;
+    if (swift::launch_forward(lv.n, plan->dtype, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+  }
+  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  return SWIFT_OK;
+}
+
+extern "C" const char* swift_status_string(swift_status s) {
+  switch (s) {
+    case SWIFT_OK:
+      return "SWIFT_OK";
+    case SWIFT_ERR_INVALID_ARG:
+      return "SWIFT_ERR_INVALID_ARG";
+    case SWIFT_ERR_UNSUPPORTED:
+      return "SWIFT_ERR_UNSUPPORTED";
+    case SWIFT_ERR_CUDA:
+      return "SWIFT_ERR_CUDA";
+    case SWIFT_ERR_OOM:
+      return "SWIFT_ERR_OOM";
+    case SWIFT_ERR_TIMEOUT:
+      return "SWIFT_ERR_TIMEOUT";
+  }
+  return "SWIFT_ERR_UNKNOWN";
+}
+
+extern "C" const char* swift_version(void) { return "swift-gb300 0.1 sm_103a"; }

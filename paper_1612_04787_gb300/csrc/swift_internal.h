@@ -1,0 +1,37 @@
+// Internal launch descriptors shared by the host API and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swift.h"
+
+namespace swift {
+
+// Everything one forward launch needs, passed by value as the kernel argument.
+struct MatchLaunch {
+  const void* ref;  // reference image (or first of ref_count sections)
+  const void* mov;  // moving image
+  long long ref_pitch, mov_pitch;    // elements between rows
+  long long ref_stride, mov_stride;  // elements between stacked sections / patches
+  int ref_h, ref_w, mov_h, mov_w;    // image sizes (section mode)
+  int ref_count;                     // sections averaged into the reference (>= 1)
+  int patch_mode;                    // 1: window b is the patch at data + b * stride
+  const int* ref_origin;             // [B][2] (y, x), section mode
+  const int* mov_origin;
+  const int* level_idx;              // [B] or null
+  int level;                         // windows of this level only (when level_idx != null)
+  long long n_windows;
+  float w;                           // whitening exponent
+  float radius2;                     // floor(r^2): background iff dy^2 + dx^2 > radius2
+  double inv_sum_a;                  // 1 / sum over the window of the 2D taper
+  const float* taper;                // [n] 1D taper
+  const float2* twiddle;             // [R2][R1] forward W_n^{j m}
+  swift_result* out;                 // [B]
+};
+
+// forward launchers (one per window size), defined in swim_forward.cu
+cudaError_t launch_forward(int n, swift_dtype dtype, const MatchLaunch& L, cudaStream_t stream);
+// radix split (R1, R2) used by the kernel for window size n; false if n is not built
+bool forward_radices(int n, int* r1, int* r2);
+
+}  // namespace swift

@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every entry point include/swift.h
+declares; argument errors come back as status codes before any CUDA work
+(so these run without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "swift.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(swift_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    fns = header_functions()
+    for name in ("swift_plan_create", "swift_plan_destroy", "swift_match_batch", "swift_status_string"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1612_04787_gb300 import _lib
+    lib = C.CDLL(_lib.LIB_PATH)
+    for name in header_functions():
+        assert hasattr(lib, name), f"{name} declared in swift.h but not exported"
+    assert set(_lib.EXPORTS) == set(header_functions())
+
+
+def test_status_strings_and_version():
+    from paper_1612_04787_gb300 import _lib
+    for code in range(6):
+        assert _lib.lib.swift_status_string(code).decode().startswith("SWIFT_")
+    assert b"sm_103a" in _lib.lib.swift_version()
+
+
+def test_argument_errors_are_reported_before_any_launch():
+    from paper_1612_04787_gb300 import _lib
+    lib = _lib.lib
+    h = C.c_void_p(1234)
+    assert lib.swift_plan_create(None, 1, 0, 0, 10, C.byref(h)) == _lib.SWIFT_ERR_INVALID_ARG
+    assert h.value is None  # *out cleared on failure
+    lv = (_lib.SwiftLevel * 1)(_lib.SwiftLevel(100, 0.5, 1, 1.0, 3.0))  # not a power of two
+    assert lib.swift_plan_create(lv, 1, 0, 0, 10, C.byref(h)) == _lib.SWIFT_ERR_INVALID_ARG
+    lv = (_lib.SwiftLevel * 1)(_lib.SwiftLevel(64, 1.5, 1, 1.0, 3.0))  # exponent outside [0, 1]
+    assert lib.swift_plan_create(lv, 1, 0, 0, 10, C.byref(h)) == _lib.SWIFT_ERR_INVALID_ARG
+    lv = (_lib.SwiftLevel * 1)(_lib.SwiftLevel(64, 0.5, 2, 0.0, 3.0))  # tukey alpha 0
+    assert lib.swift_plan_create(lv, 1, 0, 0, 10, C.byref(h)) == _lib.SWIFT_ERR_INVALID_ARG
+    lv = (_lib.SwiftLevel * 1)(_lib.SwiftLevel(1024, 0.5, 1, 1.0, 3.0))  # size not built
+    assert lib.swift_plan_create(lv, 1, 0, 0, 10, C.byref(h)) == _lib.SWIFT_ERR_UNSUPPORTED
+    lv = (_lib.SwiftLevel * 1)(_lib.SwiftLevel(64, 0.5, 1, 1.0, 3.0))
+    assert lib.swift_plan_create(lv, 0, 0, 0, 10, C.byref(h)) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_plan_create(lv, 1, 7, 0, 10, C.byref(h)) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_plan_create(lv, 1, 0, 0, 0, C.byref(h)) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_match_batch(None, None, None, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_plan_destroy(None) == _lib.SWIFT_OK
+
+
+def test_product_path_has_no_oracle_dependency():
+    pkg = os.path.join(ROOT, "paper_1612_04787_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.sub(r"#.*|//.*", "", txt).replace("the oracle", ""), f

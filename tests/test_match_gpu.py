@@ -1,0 +1,203 @@
+"""Parity of the CUDA forward match against the FP64 oracle (through the C ABI).
+
+Inputs are seeded synthetic stand-ins for the paper's ssEM sections: EM-like
+uint8 section pairs (one warped affinely and smoothly), float32 patch pairs
+with known band-limited shifts, and the 64 x 64 blurred-noise worked example.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import swim
+from parity import compare, oracle_window
+
+pytestmark = pytest.mark.gpu
+
+swift = pytest.importorskip("paper_1612_04787_gb300") if torch.cuda.is_available() else None
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+DEV = "cuda:0"
+
+
+def oracle_level(lv):
+    apod = {"none": swim.APOD_NONE, "hann": swim.APOD_HANN, "tukey": swim.APOD_TUKEY}[lv.apod]
+    return swim.Level(lv.n, lv.whiten_exponent, apod, lv.tukey_alpha, lv.snr_exclusion_radius)
+
+
+@pytest.fixture(scope="module")
+def sections():
+    a, b = synth.em_section_pair(1024, seed_content=5, seed_warp=6, seed_noise=(7, 8))
+    return a, b
+
+
+def run_sections(a, b, ro, mo, lv, dtype="u8"):
+    plan = swift.Plan([lv], dtype=dtype, max_windows=max(1, len(ro)))
+    ta = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    tb = torch.from_numpy(np.ascontiguousarray(b)).to(DEV)
+    tro = torch.from_numpy(ro.astype(np.int32)).to(DEV)
+    tmo = torch.from_numpy(mo.astype(np.int32)).to(DEV)
+    res = plan.match(ta, tb, tro, tmo)
+    torch.cuda.synchronize()
+    return swift.decode(res)
+
+
+def check_sections(a, b, ro, mo, lv, g, where):
+    olv = oracle_level(lv)
+    kinds = []
+    for i in range(len(ro)):
+        r = swim.gather(a, ro[i], lv.n)
+        m = swim.gather(b, mo[i], lv.n)
+        if r is None or m is None:
+            assert int(g["status"][i]) == swim.OUT_OF_BOUNDS
+            continue
+        ref, tied = oracle_window(m, r, olv)
+        kinds.append(compare(g, i, ref, tied, lv.n, where))
+    return kinds
+
+
+def test_noise_pair_worked_example():
+    ref, mov = synth.noise_pair(64, (-3, 5))
+    lv = swift.Level(64, 0.65, "hann", 1.0, 3.0)
+    plan = swift.Plan([lv], dtype="f32", max_windows=1)
+    tr = torch.from_numpy(ref.astype(np.float32)[None]).to(DEV)
+    tm = torch.from_numpy(mov.astype(np.float32)[None]).to(DEV)
+    g = swift.decode(plan.match(tr, tm))
+    o, tied = oracle_window(mov.astype(np.float32).astype(np.float64), ref.astype(np.float32).astype(np.float64),
+                            oracle_level(lv))
+    assert (int(g["dy"][0]), int(g["dx"][0])) == (-3, 5)
+    assert compare(g, 0, o, tied, 64, "noise pair") == "exact"
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("w", [0.0, 0.65, 1.0])
+def test_sections_u8_parity(sections, n, w):
+    a, b = sections
+    rng = np.random.default_rng(n + int(100 * w))
+    cnt = {64: 48, 128: 32, 256: 16}[n]
+    ro = synth.random_origins(cnt, 1024, 1024, n, seed=n + 1)
+    mo = np.clip(ro + rng.integers(-12, 13, ro.shape), 0, 1024 - n).astype(np.int32)
+    lv = swift.Level(n, w, "hann", 1.0, 3.0)
+    g = run_sections(a, b, ro, mo, lv)
+    kinds = check_sections(a, b, ro, mo, lv, g, f"n={n} w={w}")
+    assert kinds.count("exact") >= len(kinds) - 2
+
+
+@pytest.mark.parametrize("apod,alpha", [("none", 1.0), ("tukey", 0.5), ("tukey", 0.25)])
+def test_taper_variants(sections, apod, alpha):
+    a, b = sections
+    n = 128
+    ro = synth.random_origins(12, 1024, 1024, n, seed=31)
+    mo = ro.copy()
+    lv = swift.Level(n, 0.5, apod, alpha, 2.5)
+    g = run_sections(a, b, ro, mo, lv)
+    check_sections(a, b, ro, mo, lv, g, f"{apod}({alpha})")
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("w", [0.0, 0.35, 1.0])
+def test_exact_circular_shift_recovered(n, w):
+    rng = np.random.default_rng(n)
+    B = 6
+    ref = rng.uniform(0, 255, (B, n, n)).astype(np.float32)
+    d = rng.integers(-n // 2, n // 2, (B, 2))
+    mov = np.stack([np.roll(ref[i], tuple(d[i]), axis=(0, 1)) for i in range(B)])
+    lv = swift.Level(n, w, "none", 1.0, 3.0)
+    plan = swift.Plan([lv], dtype="f32", max_windows=B)
+    g = swift.decode(plan.match(torch.from_numpy(ref).to(DEV), torch.from_numpy(mov).to(DEV)))
+    np.testing.assert_array_equal(g["dy"], d[:, 0])
+    np.testing.assert_array_equal(g["dx"], d[:, 1])
+    if w == 1.0:
+        np.testing.assert_allclose(g["peak"], 1.0 - 1.0 / n ** 2, rtol=1e-4)
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_shifted_patches_f32(sections, n):
+    a, _ = sections
+    ref, mov, d = synth.shifted_patches(a, n, 8, seed=40 + n)
+    lv = swift.Level(n, 0.65, "hann", 1.0, 3.0)
+    plan = swift.Plan([lv], dtype="f32", max_windows=8)
+    g = swift.decode(plan.match(torch.from_numpy(ref).to(DEV), torch.from_numpy(mov).to(DEV)))
+    olv = oracle_level(lv)
+    for i in range(8):
+        o, tied = oracle_window(mov[i].astype(np.float64), ref[i].astype(np.float64), olv)
+        compare(g, i, o, tied, n, f"patch n={n}")
+        # and the known shift is recovered to within a pixel
+        assert abs(g["sy"][i] - d[i, 0]) < 1.0 and abs(g["sx"][i] - d[i, 1]) < 1.0
+
+
+def test_projection_reference(sections):
+    a, b = sections
+    n = 128
+    stack = np.stack([a, np.roll(a, 1, axis=1), np.roll(a, -1, axis=0)])
+    ro = synth.random_origins(6, 1024, 1024, n, seed=3, margin=2)
+    lv = swift.Level(n, 0.65, "hann", 1.0, 3.0)
+    plan = swift.Plan([lv], dtype="u8", max_windows=6)
+    g = swift.decode(plan.match(torch.from_numpy(stack).to(DEV), torch.from_numpy(b).to(DEV),
+                                torch.from_numpy(ro).to(DEV), torch.from_numpy(ro).to(DEV)))
+    olv = oracle_level(lv)
+    for i in range(6):
+        r = swim.project(list(stack), ro[i], n)
+        m = swim.gather(b, ro[i], n)
+        o, tied = oracle_window(m, r.astype(np.float32).astype(np.float64), olv)
+        compare(g, i, o, tied, n, "projection")
+
+
+def test_mixed_levels_one_call(sections):
+    a, b = sections
+    a2, b2 = synth.box_downsample(a, 2), synth.box_downsample(b, 2)
+    a4, b4 = synth.box_downsample(a, 4), synth.box_downsample(b, 4)
+    levels = [swift.Level(64, 0.5), swift.Level(128, 0.65), swift.Level(256, 0.8)]
+    imgs_a, imgs_b = [a4, a2, a], [b4, b2, b]
+    o = [synth.grid_origins(img.shape[0], lv.n, lv.n // 2)[::5] for img, lv in zip(imgs_a, levels)]
+    lvl = np.concatenate([np.full(len(x), k, np.int32) for k, x in enumerate(o)])
+    org = np.concatenate(o).astype(np.int32)
+    perm = np.random.default_rng(0).permutation(len(org))
+    org, lvl = org[perm], lvl[perm]
+    plan = swift.Plan(levels, dtype="u8", max_windows=len(org))
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)  # noqa: E731
+    g = swift.decode(plan.match([T(x) for x in imgs_a], [T(x) for x in imgs_b], T(org), T(org), level=T(lvl)))
+    for i in range(len(org)):
+        lv = levels[lvl[i]]
+        r = swim.gather(imgs_a[lvl[i]], org[i], lv.n)
+        m = swim.gather(imgs_b[lvl[i]], org[i], lv.n)
+        ref, tied = oracle_window(m, r, oracle_level(lv))
+        compare(g, i, ref, tied, lv.n, f"mixed level {lvl[i]}")
+
+
+def test_status_codes_and_empty_batch():
+    n = 64
+    lv = swift.Level(n, 0.65, "hann")
+    sec = torch.from_numpy(np.random.default_rng(1).integers(0, 256, (200, 300)).astype(np.uint8)).to(DEV)
+    flat = torch.full((200, 300), 9, dtype=torch.uint8, device=DEV)
+    plan = swift.Plan([lv], dtype="u8", max_windows=4)
+    o = torch.tensor([[0, 0], [150, 10], [10, 250], [136, 236]], dtype=torch.int32, device=DEV)
+    g = swift.decode(plan.match(sec, sec, o, o))
+    assert list(g["status"]) == [0, 1, 1, 0]
+    g = swift.decode(plan.match(flat, sec, o, o))
+    assert list(g["status"]) == [2, 1, 1, 2]
+    empty = torch.zeros((0, 2), dtype=torch.int32, device=DEV)
+    out = plan.match(sec, sec, empty, empty)
+    assert out.shape == (0, 8)
+    fplan = swift.Plan([lv], dtype="f32", max_windows=2)
+    p = torch.randn(2, n, n, device=DEV)
+    q = p.clone()
+    q[1, 5, 7] = float("nan")
+    g = swift.decode(fplan.match(p, q))
+    assert list(g["status"]) == [0, 3]
+    with pytest.raises(swift.SwiftError):
+        plan.match(sec, sec, torch.zeros((5, 2), dtype=torch.int32, device=DEV),
+                   torch.zeros((5, 2), dtype=torch.int32, device=DEV))  # beyond max_windows
+
+
+def test_deterministic(sections):
+    a, b = sections
+    n = 256
+    ro = synth.random_origins(16, 1024, 1024, n, seed=9)
+    lv = swift.Level(n, 0.65)
+    plan = swift.Plan([lv], dtype="u8", max_windows=16)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)  # noqa: E731
+    r1 = plan.match(T(a), T(b), T(ro), T(ro)).clone()
+    r2 = plan.match(T(a), T(b), T(ro), T(ro))
+    assert torch.equal(r1, r2)
