@@ -201,6 +201,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (961 windows each)")
     ap.add_argument("--oracle-sample", type=int, default=961)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--windows", type=int, default=0,
+                    help="use only the first K windows of the grid (small profiling cases)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -239,6 +241,8 @@ def main():
     import paper_1612_04787_gb300 as swift
 
     secs, org = make_inputs(args.pairs)
+    if args.windows > 0:
+        org = org[: args.windows]
     B1 = len(org)
     plan = swift.Plan([swift.Level(N_WIN, W_EXP, "hann", 1.0, RADIUS)], dtype="u8", max_windows=B1)
     d_secs = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in secs]

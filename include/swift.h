@@ -57,7 +57,9 @@ enum {
   SWIFT_WIN_OK = 0,
   SWIFT_WIN_OUT_OF_BOUNDS = 1, /* a window leaves its image                     */
   SWIFT_WIN_FLAT = 2,          /* all pixels of either window are equal         */
-  SWIFT_WIN_NONFINITE = 3      /* a NaN or infinity in either (float) window    */
+  SWIFT_WIN_NONFINITE = 3,     /* a NaN or infinity in either (float) window    */
+  SWIFT_WIN_TIMEOUT = 4        /* a staged window load did not complete within
+                                  its bounded wait; outputs are not valid      */
 };
 
 /* One matching configuration (one pyramid level), Sec. III:
@@ -67,7 +69,8 @@ enum {
  *                        0 = plain correlation, 1 = phase-only correlation
  *   apod, tukey_alpha    taper (alpha in (0, 1], used by TUKEY only)
  *   snr_exclusion_radius pixels within this wrapped Euclidean distance of the
- *                        peak are left out of the SNR background (>= 0)      */
+ *                        peak are left out of the SNR background; in
+ *                        [0, n/4)                                            */
 typedef struct {
   int32_t n;
   float whiten_exponent;

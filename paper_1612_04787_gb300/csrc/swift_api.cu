@@ -52,7 +52,19 @@ struct swift_plan_s {
   float* taper[kMaxLevels] = {};
   double inv_sum_a[kMaxLevels] = {};
   float2* twiddle[3] = {};
+  // streaming forward path: per-level choice and its workspace
+  int stream_level[kMaxLevels] = {};
+  void* work = nullptr;
+  long long work_windows = 0;  // capacity (windows of the largest streamed size)
 };
+
+namespace {
+// windows per slice of the streaming path (bounds its workspace)
+constexpr long long kStreamSlice = 2048;
+// default forward schedule: 256 x 256 and 128 x 128 windows stream their
+// intermediates through the workspace; 64 x 64 windows use the fused kernel
+bool default_stream(int n) { return n >= 128; }
+}  // namespace
 
 static swift_status release(swift_plan p) {
   if (!p) return SWIFT_OK;
@@ -63,6 +75,7 @@ static swift_status release(swift_plan p) {
     if (p->taper[l]) cudaFree(p->taper[l]);
   for (int i = 0; i < 3; ++i)
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
+  if (p->work) cudaFree(p->work);
   if (cur != p->device) cudaSetDevice(cur);
   delete p;
   return SWIFT_OK;
@@ -82,7 +95,7 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
     if (lv.apod != SWIFT_APOD_NONE && lv.apod != SWIFT_APOD_HANN && lv.apod != SWIFT_APOD_TUKEY)
       return SWIFT_ERR_INVALID_ARG;
     if (lv.apod == SWIFT_APOD_TUKEY && !(lv.tukey_alpha > 0.f && lv.tukey_alpha <= 1.f)) return SWIFT_ERR_INVALID_ARG;
-    if (!(lv.snr_exclusion_radius >= 0.f) || !(lv.snr_exclusion_radius < 1e4f)) return SWIFT_ERR_INVALID_ARG;
+    if (!(lv.snr_exclusion_radius >= 0.f) || !(lv.snr_exclusion_radius < 0.25f * lv.n)) return SWIFT_ERR_INVALID_ARG;
     if (size_slot(lv.n) < 0) return SWIFT_ERR_UNSUPPORTED;
   }
   swift_plan p = new (std::nothrow) swift_plan_s();
@@ -131,6 +144,23 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
         cudaGetLastError();
         return SWIFT_ERR_OOM;
       }
+    }
+  }
+  // workspace of the streaming forward path
+  size_t per = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    p->stream_level[l] = default_stream(levels[l].n) ? 1 : 0;
+    if (p->stream_level[l]) {
+      const size_t b = swift::stream_bytes_per_window(levels[l].n);
+      per = b > per ? b : per;
+    }
+  }
+  if (per > 0) {
+    p->work_windows = max_windows < kStreamSlice ? max_windows : kStreamSlice;
+    if (cudaMalloc(&p->work, per * p->work_windows + 4096) != cudaSuccess) {
+      release(p);
+      cudaGetLastError();
+      return SWIFT_ERR_OOM;
     }
   }
   *out = p;
@@ -198,7 +228,19 @@ extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* ba
     L.taper = plan->taper[l];
     L.twiddle = plan->twiddle[size_slot(lv.n)];
     L.out = out;
-    if (swift::launch_forward(lv.n, plan->dtype, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+    if (plan->stream_level[l]) {
+      for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
+        const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
+        const swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
+        if (swift::launch_stream(lv.n, plan->dtype, L, W, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+      }
+      continue;
+    }
+    const bool bulk = plan->dtype == SWIFT_IN_U8 && !pm && ri.count == 1 &&
+                      (reinterpret_cast<uintptr_t>(ri.data) % 16) == 0 &&
+                      (reinterpret_cast<uintptr_t>(mi.data) % 16) == 0 && ri.pitch % 16 == 0 &&
+                      mi.pitch % 16 == 0 && ri.width % 16 == 0 && mi.width % 16 == 0;
+    if (swift::launch_forward(lv.n, plan->dtype, bulk, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
   }
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   return SWIFT_OK;

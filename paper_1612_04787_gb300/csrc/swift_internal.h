@@ -29,8 +29,25 @@ struct MatchLaunch {
   swift_result* out;                 // [B]
 };
 
+// Workspace of the streaming forward path for one slice of windows.
+struct StreamWork {
+  float4* stats;             // [S] (mu_m, mu_r, status bits, unused)
+  float2* zr;                // [S][n][n] row spectra; reused for the match response (float [n][n])
+  float2* h;                 // [S][n][n/2] inverse-column output
+  unsigned long long* part;  // [S][blocks][3] block argmax key, FP64 sum of s, FP64 sum of s^2
+  long long b0;              // first window of the slice
+  long long count;           // windows in the slice
+};
+
+// streaming forward path (swim_stream.cu): bytes of workspace per window, launch of one slice
+size_t stream_bytes_per_window(int n);
+StreamWork stream_carve(void* base, long long capacity, int n, long long b0, long long count);
+cudaError_t launch_stream(int n, swift_dtype dtype, const MatchLaunch& L, const StreamWork& W, cudaStream_t stream);
+
 // forward launchers (one per window size), defined in swim_forward.cu
-cudaError_t launch_forward(int n, swift_dtype dtype, const MatchLaunch& L, cudaStream_t stream);
+// bulk: stage uint8 section rows with cp.async.bulk (needs 16-byte aligned
+// base pointers, pitches and widths, and a single reference section)
+cudaError_t launch_forward(int n, swift_dtype dtype, bool bulk, const MatchLaunch& L, cudaStream_t stream);
 // radix split (R1, R2) used by the kernel for window size n; false if n is not built
 bool forward_radices(int n, int* r1, int* r2);
 

@@ -1,0 +1,108 @@
+// Launchers of the streaming forward path (five kernels per slice of windows).
+#include "swim_stream.cuh"
+
+namespace swift {
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+template <int N>
+size_t part_blocks() {
+  return StreamGeom<N>::NB3;
+}
+
+size_t blocks3(int n) {
+  switch (n) {
+    case 64:
+      return StreamGeom<64>::NB3;
+    case 128:
+      return StreamGeom<128>::NB3;
+    default:
+      return StreamGeom<256>::NB3;
+  }
+}
+
+template <int N, typename TIn>
+constexpr size_t rows_smem() {
+  using G = StreamGeom<N>;
+  return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * N + 2 * sizeof(TIn) * G::RB * N;
+}
+template <int N>
+constexpr size_t cols_smem() {
+  using G = StreamGeom<N>;
+  return sizeof(float2) * (N * (2 * G::CB + 8) + 2 * N);
+}
+template <int N>
+constexpr size_t irows_smem() {
+  using G = StreamGeom<N>;
+  return sizeof(float2) * (G::PB * G::RS + N);
+}
+
+// dynamic shared-memory opt-in, once per device and kernel
+template <typename K>
+cudaError_t smem_optin(K kern, size_t bytes, unsigned& done_mask, int dev) {
+  if (dev < 32 && (done_mask & (1u << dev))) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess && dev < 32) done_mask |= 1u << dev;
+  return e;
+}
+
+template <int N, typename TIn>
+cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st) {
+  using G = StreamGeom<N>;
+  const unsigned S = static_cast<unsigned>(W.count);
+  if (S == 0) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static unsigned m1 = 0, m2 = 0, m3 = 0;
+  if ((e = smem_optin(stream_rows_kernel<N, TIn>, rows_smem<N, TIn>(), m1, dev)) != cudaSuccess) return e;
+  if ((e = smem_optin(stream_cols_kernel<N>, cols_smem<N>(), m2, dev)) != cudaSuccess) return e;
+  if ((e = smem_optin(stream_irows_kernel<N>, irows_smem<N>(), m3, dev)) != cudaSuccess) return e;
+  stream_stats_kernel<N, TIn><<<S, 256, 0, st>>>(L, W);
+  stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+  stream_cols_kernel<N><<<S * G::NB2, 256, cols_smem<N>(), st>>>(L, W);
+  stream_irows_kernel<N><<<S * G::NB3, 256, irows_smem<N>(), st>>>(L, W);
+  stream_final_kernel<N><<<S, 32, 0, st>>>(L, W);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t stream_bytes_per_window(int n) {
+  const size_t nn = static_cast<size_t>(n) * n;
+  return sizeof(float4) + sizeof(float2) * nn + sizeof(float2) * nn / 2 + 3 * sizeof(unsigned long long) * blocks3(n);
+}
+
+StreamWork stream_carve(void* base, long long capacity, int n, long long b0, long long count) {
+  const size_t nn = static_cast<size_t>(n) * n;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  StreamWork W;
+  W.stats = reinterpret_cast<float4*>(p);
+  p += align256(sizeof(float4) * capacity);
+  W.zr = reinterpret_cast<float2*>(p);
+  p += align256(sizeof(float2) * nn * capacity);
+  W.h = reinterpret_cast<float2*>(p);
+  p += align256(sizeof(float2) * nn / 2 * capacity);
+  W.part = reinterpret_cast<unsigned long long*>(p);
+  W.b0 = b0;
+  W.count = count;
+  return W;
+}
+
+cudaError_t launch_stream(int n, swift_dtype dtype, const MatchLaunch& L, const StreamWork& W, cudaStream_t st) {
+  const bool u8 = dtype == SWIFT_IN_U8;
+  switch (n) {
+    case 64:
+      return u8 ? launch_n<64, uint8_t>(L, W, st) : launch_n<64, float>(L, W, st);
+    case 128:
+      return u8 ? launch_n<128, uint8_t>(L, W, st) : launch_n<128, float>(L, W, st);
+    case 256:
+      return u8 ? launch_n<256, uint8_t>(L, W, st) : launch_n<256, float>(L, W, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace swift

@@ -1,0 +1,636 @@
+// Streaming forward matching: five kernels of small independent CTAs that
+// pass each window's intermediates through a plan-owned workspace.
+//
+//   K0 stats     one CTA per window: bounds, flat / non-finite checks and the
+//                taper-weighted means of both windows
+//   K1 rows      (window, row block): apodise z = m' + i r', 1D DFT of each row
+//                -> Zr[y][kx]
+//   K2 columns   (window, column block closed under kx -> -kx): 1D DFT of the
+//                columns, Hermitian unpack of M and R, C = M conj(R),
+//                whitening G = C |C|^-w / n^2 (G[0,0] = 0), inverse DFT of the
+//                columns kx in [0, n/2] -> H[y][kx] (kx = 0 carries kx = n/2
+//                as its imaginary part)
+//   K3 inv rows  (window, block of row pairs): rows y and y + n/2 of H form one
+//                complex row (Hermitian completion), inverse DFT -> match
+//                response s for both rows; block argmax
+//   K4 finalize  one CTA per window: global argmax, SNR over the background
+//                outside the exclusion disc, subpixel parabola fit, result
+//
+// Every CTA works alone (no clusters, no cross-CTA waits), so many CTAs share
+// an SM and hide each other's latency.  1D transforms use the same in-place
+// two-pass radix scheme as the fused kernel (pass A strided, pass B on
+// contiguous blocks with twiddles; "rho" digit-reversed order in between).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dft_regs.cuh"
+#include "swim_kernel.cuh"
+#include "swift_internal.h"
+
+namespace swift {
+
+constexpr int kStatusSkip = -1;  // window of another level: no result written here
+
+template <int N>
+struct StreamGeom {
+  static constexpr int R1 = N == 64 ? 8 : 16;
+  static constexpr int R2 = N / R1;
+  static constexpr int T = 256;
+  static constexpr int RS = N == 256 ? 272 : (N == 128 ? 152 : 72);  // padded row stride
+  static constexpr int RB = T / R2;        // K1: rows per CTA
+  static constexpr int CB = 128 / R2;      // K2: kx values (plus partners) per CTA
+  static constexpr int NB2 = N / (2 * CB);
+  static constexpr int PB = (T / R2) < (N / 2) ? (T / R2) : (N / 2);  // K3: row pairs per CTA
+  static constexpr int NB3 = (N / 2) / PB;
+  static_assert(R1 * R2 == N, "radix");
+  static_assert(RS >= N + N / R2, "padding");
+  static __device__ __forceinline__ int phys(int p) { return p + p / R2; }
+  static __device__ __forceinline__ int rho(int k) { return k / R1 + R2 * (k % R1); }
+  // K2 column ownership (same scheme as the fused kernel with C = NB2, Q = CB)
+  static __device__ __forceinline__ int kx_of(int b, int lc) {
+    if (lc < CB) return CB * b + lc;
+    if (b == 0 && lc == CB) return N / 2;
+    return N - (CB * b + lc - CB);
+  }
+};
+
+
+__device__ __forceinline__ int stat_status(const float4& s) { return __float_as_int(s.z); }
+
+// ---------------------------------------------------------------------------
+// K0: statistics
+// ---------------------------------------------------------------------------
+template <int N, typename TIn>
+__global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, const StreamWork W) {
+  const long long s = blockIdx.x;
+  const long long b = W.b0 + s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ float tap[N];
+  __shared__ double red[8][2];
+  __shared__ float mred[8][4];
+  __shared__ int bred[8];
+  auto put = [&](int status, float mm, float mr) {
+    if (tid == 0) W.stats[s] = make_float4(mm, mr, __int_as_float(status), 0.f);
+  };
+  if (L.level_idx != nullptr && __ldg(L.level_idx + b) != L.level) {
+    put(kStatusSkip, 0.f, 0.f);
+    return;
+  }
+  const TIn* mbase;
+  const TIn* rbase;
+  long long mpitch, rpitch;
+  if (L.patch_mode) {
+    mbase = static_cast<const TIn*>(L.mov) + b * L.mov_stride;
+    rbase = static_cast<const TIn*>(L.ref) + b * L.ref_stride;
+    mpitch = rpitch = N;
+  } else {
+    const int my = __ldg(L.mov_origin + 2 * b), mx = __ldg(L.mov_origin + 2 * b + 1);
+    const int ry = __ldg(L.ref_origin + 2 * b), rx = __ldg(L.ref_origin + 2 * b + 1);
+    if (my < 0 || mx < 0 || my > L.mov_h - N || mx > L.mov_w - N || ry < 0 || rx < 0 || ry > L.ref_h - N ||
+        rx > L.ref_w - N) {
+      put(SWIFT_WIN_OUT_OF_BOUNDS, 0.f, 0.f);
+      return;
+    }
+    mbase = static_cast<const TIn*>(L.mov) + static_cast<long long>(my) * L.mov_pitch + mx;
+    rbase = static_cast<const TIn*>(L.ref) + static_cast<long long>(ry) * L.ref_pitch + rx;
+    mpitch = L.mov_pitch;
+    rpitch = L.ref_pitch;
+  }
+  for (int i = tid; i < N; i += 256) tap[i] = L.taper[i];
+  __syncthreads();
+  const float inv_k = 1.0f / static_cast<float>(L.ref_count);
+  float sm = 0.f, sr = 0.f, mn_m = 3.4e38f, mx_m = -3.4e38f, mn_r = 3.4e38f, mx_r = -3.4e38f;
+  int bad = 0;
+  auto accum = [&](float a, float mv, float rv) {
+    sm = fmaf(a, mv, sm);
+    sr = fmaf(a, rv, sr);
+    mn_m = fminf(mn_m, mv);
+    mx_m = fmaxf(mx_m, mv);
+    mn_r = fminf(mn_r, rv);
+    mx_r = fmaxf(mx_r, rv);
+    if constexpr (sizeof(TIn) == 4) bad |= !(fabsf(mv) <= 3.4e38f) | !(fabsf(rv) <= 3.4e38f);
+  };
+  // 16-byte vector loads when both windows' rows are 16-byte aligned
+  constexpr int VEC = 16 / static_cast<int>(sizeof(TIn));
+  const bool vec = L.ref_count == 1 && ((reinterpret_cast<uintptr_t>(mbase) | reinterpret_cast<uintptr_t>(rbase) |
+                                         static_cast<uintptr_t>(mpitch * sizeof(TIn)) |
+                                         static_cast<uintptr_t>(rpitch * sizeof(TIn))) & 15) == 0;
+  if (vec) {
+    for (int e = tid; e < N * N / VEC; e += 256) {
+      const int y = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
+      const uint4 mq = __ldg(reinterpret_cast<const uint4*>(mbase + y * mpitch + x0));
+      const uint4 rq = __ldg(reinterpret_cast<const uint4*>(rbase + y * rpitch + x0));
+      const float ay = tap[y];
+      if constexpr (sizeof(TIn) == 1) {
+        const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w}, rw[4] = {rq.x, rq.y, rq.z, rq.w};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float mv = static_cast<float>((mw[k >> 2] >> (8 * (k & 3))) & 0xffu);
+          const float rv = static_cast<float>((rw[k >> 2] >> (8 * (k & 3))) & 0xffu);
+          accum(ay * tap[x0 + k], mv, rv);
+        }
+      } else {
+        const float mf[4] = {__uint_as_float(mq.x), __uint_as_float(mq.y), __uint_as_float(mq.z),
+                             __uint_as_float(mq.w)};
+        const float rf[4] = {__uint_as_float(rq.x), __uint_as_float(rq.y), __uint_as_float(rq.z),
+                             __uint_as_float(rq.w)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) accum(ay * tap[x0 + k], mf[k], rf[k]);
+      }
+    }
+  } else {
+    for (int e = tid; e < N * N; e += 256) {  // consecutive threads, consecutive x
+      const int y = e / N, x = e % N;
+      const TIn* rrow = rbase + y * rpitch;
+      const float mv = load_px<TIn>(mbase + y * mpitch + x);
+      float rv = load_px<TIn>(rrow + x);
+      for (int k = 1; k < L.ref_count; ++k) rv += load_px<TIn>(rrow + k * L.ref_stride + x);
+      if (L.ref_count > 1) rv *= inv_k;
+      accum(tap[y] * tap[x], mv, rv);
+    }
+  }
+  double dm = warp_sum_f64(static_cast<double>(sm)), dr = warp_sum_f64(static_cast<double>(sr));
+  float a0 = warp_min_f32(mn_m), a1 = warp_max_f32(mx_m), a2 = warp_min_f32(mn_r), a3 = warp_max_f32(mx_r);
+  int bb = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    red[warp][0] = dm;
+    red[warp][1] = dr;
+    mred[warp][0] = a0;
+    mred[warp][1] = a1;
+    mred[warp][2] = a2;
+    mred[warp][3] = a3;
+    bred[warp] = bb;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tm = 0, tr = 0;
+    float e = 3.4e38f, f = -3.4e38f, g = 3.4e38f, h = -3.4e38f;
+    int nb = 0;
+    for (int v = 0; v < 8; ++v) {
+      tm += red[v][0];
+      tr += red[v][1];
+      e = fminf(e, mred[v][0]);
+      f = fmaxf(f, mred[v][1]);
+      g = fminf(g, mred[v][2]);
+      h = fmaxf(h, mred[v][3]);
+      nb |= bred[v];
+    }
+    const int st = nb ? SWIFT_WIN_NONFINITE : ((e == f || g == h) ? SWIFT_WIN_FLAT : SWIFT_WIN_OK);
+    W.stats[s] = make_float4(static_cast<float>(tm * L.inv_sum_a), static_cast<float>(tr * L.inv_sum_a),
+                             __int_as_float(st), 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1: row transforms of z = m' + i r'
+// ---------------------------------------------------------------------------
+template <int N, typename TIn>
+__global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, const StreamWork W) {
+  using G = StreamGeom<N>;
+  constexpr int R1 = G::R1, R2 = G::R2, RB = G::RB, RS = G::RS, T = G::T;
+  constexpr int KB = (RB * R1 + T - 1) / T;
+  const long long s = blockIdx.x / (N / RB);
+  const int rb = blockIdx.x % (N / RB);
+  const long long b = W.b0 + s;
+  const int tid = threadIdx.x;
+  const float4 st = W.stats[s];
+  if (stat_status(st) != SWIFT_WIN_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* slab = reinterpret_cast<float2*>(smem_raw);  // [RB][RS]
+  float2* twid = slab + RB * RS;
+  float* tap = reinterpret_cast<float*>(twid + N);
+  // raw rows: uint8/float32 moving and reference; the reference of a K-section
+  // model (or unaligned rows) is staged as float in rfstage, which aliases the slab
+  TIn* mstage = reinterpret_cast<TIn*>(tap + N);
+  TIn* rstage = mstage + RB * N;
+  float* rfstage = reinterpret_cast<float*>(slab);
+  for (int i = tid; i < N; i += T) {
+    twid[i] = L.twiddle[i];
+    tap[i] = L.taper[i];
+  }
+  const TIn* mbase;
+  const TIn* rbase;
+  long long mpitch, rpitch;
+  if (L.patch_mode) {
+    mbase = static_cast<const TIn*>(L.mov) + b * L.mov_stride;
+    rbase = static_cast<const TIn*>(L.ref) + b * L.ref_stride;
+    mpitch = rpitch = N;
+  } else {
+    mbase = static_cast<const TIn*>(L.mov) + static_cast<long long>(__ldg(L.mov_origin + 2 * b)) * L.mov_pitch +
+            __ldg(L.mov_origin + 2 * b + 1);
+    rbase = static_cast<const TIn*>(L.ref) + static_cast<long long>(__ldg(L.ref_origin + 2 * b)) * L.ref_pitch +
+            __ldg(L.ref_origin + 2 * b + 1);
+    mpitch = L.mov_pitch;
+    rpitch = L.ref_pitch;
+  }
+  mbase += static_cast<long long>(rb * RB) * mpitch;
+  rbase += static_cast<long long>(rb * RB) * rpitch;
+  // stage the block's RB rows of both windows: 16-byte vector loads when aligned
+  constexpr int VEC = 16 / static_cast<int>(sizeof(TIn));
+  constexpr int NV = RB * N / VEC;  // vectors per image
+  const bool vec = L.ref_count == 1 && ((reinterpret_cast<uintptr_t>(mbase) | reinterpret_cast<uintptr_t>(rbase) |
+                                         static_cast<uintptr_t>(mpitch * sizeof(TIn)) |
+                                         static_cast<uintptr_t>(rpitch * sizeof(TIn))) & 15) == 0;
+  if (vec) {
+    uint4 q[2 * ((NV + T - 1) / T)];
+#pragma unroll
+    for (int i = 0; i < (NV + T - 1) / T; ++i) {
+      const int e = tid + i * T;
+      if (NV % T == 0 || e < NV) {
+        const int r = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
+        q[2 * i] = __ldg(reinterpret_cast<const uint4*>(mbase + r * mpitch + x0));
+        q[2 * i + 1] = __ldg(reinterpret_cast<const uint4*>(rbase + r * rpitch + x0));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < (NV + T - 1) / T; ++i) {
+      const int e = tid + i * T;
+      if (NV % T == 0 || e < NV) {
+        reinterpret_cast<uint4*>(mstage)[e] = q[2 * i];
+        reinterpret_cast<uint4*>(rstage)[e] = q[2 * i + 1];
+      }
+    }
+  } else {
+    const float inv_k = 1.0f / static_cast<float>(L.ref_count);
+    for (int e = tid; e < RB * N; e += T) {
+      const int r = e / N, x = e % N;
+      mstage[e] = static_cast<TIn>(load_px<TIn>(mbase + r * mpitch + x));
+      float rv = load_px<TIn>(rbase + r * rpitch + x);
+      if (L.ref_count > 1) {
+        for (int k = 1; k < L.ref_count; ++k) rv += load_px<TIn>(rbase + k * L.ref_stride + r * rpitch + x);
+        rv *= inv_k;
+      }
+      rfstage[e] = rv;
+    }
+  }
+  __syncthreads();
+  // pass A: thread (line, j) takes x = j + R2 m of row rb*RB + line
+  const int line = tid / R2, j = tid % R2;
+  const int y = rb * RB + line;
+  float mv[R1], rv[R1];
+#pragma unroll
+  for (int m = 0; m < R1; ++m) {
+    const int e = line * N + j + R2 * m;
+    mv[m] = static_cast<float>(mstage[e]);
+    rv[m] = vec ? static_cast<float>(rstage[e]) : rfstage[e];
+  }
+  if (!vec) __syncthreads();  // rfstage aliases the slab written below
+  {
+    const float ay = tap[y];
+    float2 v[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+      const float a = ay * tap[j + R2 * m];
+      v[m] = make_float2(a * (mv[m] - st.x), a * (rv[m] - st.y));
+    }
+    dft<R1, -1>(v);
+    float2* row = slab + line * RS;
+#pragma unroll
+    for (int q = 0; q < R1; ++q) row[G::phys(j + R2 * q)] = v[q];
+  }
+  __syncthreads();
+  // pass B: thread (line, k1) -> X[k1 + R1 k2], written to Zr[y][kx]
+#pragma unroll
+  for (int i = 0; i < KB; ++i) {
+    const int task = tid + i * T;
+    const int ln = task / R1, k1 = task % R1;
+    const float2* row = slab + ln * RS;
+    float2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      const float2 x = row[G::phys(R2 * k1 + n2)];
+      v[n2] = n2 == 0 ? x : cmul(x, twid[n2 * R1 + k1]);
+    }
+    dft<R2, -1>(v);
+    float2* zrow = W.zr + (s * N + rb * RB + ln) * N;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) zrow[k1 + R1 * k2] = v[k2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: column transforms, unpack, whitening, inverse column transforms
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) stream_cols_kernel(const MatchLaunch L, const StreamWork W) {
+  using G = StreamGeom<N>;
+  constexpr int R1 = G::R1, R2 = G::R2, CB = G::CB, T = G::T;
+  constexpr int LINES = 2 * CB;
+  constexpr int LS = LINES + 8;  // padded row stride of the column slab
+  const long long s = blockIdx.x / G::NB2;
+  const int cb = blockIdx.x % G::NB2;
+  const int tid = threadIdx.x;
+  if (stat_status(W.stats[s]) != SWIFT_WIN_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* slab = reinterpret_cast<float2*>(smem_raw);  // [ky][lc], row stride LS
+  float2* dcbuf = slab + N * LS;
+  float2* twid = dcbuf + N;
+  for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
+  // gather columns kx(lc) of Zr (rows are contiguous in kx)
+  const float2* zr = W.zr + s * N * N;
+  {
+    constexpr int K = N * LINES / T;
+    const int lc = tid % LINES, ky0 = tid / LINES;
+    const int kx = G::kx_of(cb, lc);
+    float2 q[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) q[i] = __ldcs(zr + (ky0 + i * (T / LINES)) * N + kx);
+#pragma unroll
+    for (int i = 0; i < K; ++i) slab[(ky0 + i * (T / LINES)) * LS + lc] = q[i];
+  }
+  __syncthreads();
+  // column pass A (rows j + R2 m), in place
+  constexpr int TA = LINES * R2, TB = LINES * R1;
+#pragma unroll
+  for (int i = 0; i < (TA + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if (TA % T != 0 && task >= TA) break;
+    const int j = task / LINES, lc = task % LINES;
+    float2 v[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) v[m] = slab[(j + R2 * m) * LS + lc];
+    dft<R1, -1>(v);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) slab[(j + R2 * q) * LS + lc] = v[q];
+  }
+  __syncthreads();
+  // column pass B (rows R2 k1 + n2), in place: rho order
+#pragma unroll
+  for (int i = 0; i < (TB + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if (TB % T != 0 && task >= TB) break;
+    const int k1 = task / LINES, lc = task % LINES;
+    float2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      const float2 x = slab[(R2 * k1 + n2) * LS + lc];
+      v[n2] = n2 == 0 ? x : cmul(x, twid[n2 * R1 + k1]);
+    }
+    dft<R2, -1>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) slab[(R2 * k1 + k2) * LS + lc] = v[k2];
+  }
+  __syncthreads();
+  // unpack + whiten + inverse pass B' on lc < CB (kx = CB*cb + lc)
+  const float half_w = -0.5f * L.w;
+  const float inv_n2 = 1.0f / (static_cast<float>(N) * static_cast<float>(N));
+  constexpr int TBh = CB * R1, TAh = CB * R2;
+#pragma unroll
+  for (int i = 0; i < (TBh + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if (TBh % T != 0 && task >= TBh) break;
+    const int k1 = task / CB, lc = task % CB;
+    const bool dc_col = (cb == 0 && lc == 0);
+    const int plc = dc_col ? 0 : lc + CB;
+    float2 v[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int ky = k1 + R1 * k2;
+      const int nky = (N - ky) & (N - 1);
+      const float2 a = slab[(R2 * k1 + k2) * LS + lc];
+      const float2 bb = slab[G::rho(nky) * LS + plc];
+      const float2 c = make_float2(0.5f * fmaf(a.x, bb.y, a.y * bb.x),
+                                   0.25f * ((a.x * a.x + a.y * a.y) - (bb.x * bb.x + bb.y * bb.y)));
+      const float mag2 = fmaf(c.x, c.x, c.y * c.y);
+      const float sc = mag2 > 0.f ? exp2f(half_w * log2f(mag2)) * inv_n2 : 0.f;
+      float2 g = make_float2(c.x * sc, c.y * sc);
+      if (dc_col) {
+        const float2 a2 = slab[(R2 * k1 + k2) * LS + CB];
+        const float2 b2 = slab[G::rho(nky) * LS + CB];
+        const float2 c2 = make_float2(0.5f * fmaf(a2.x, b2.y, a2.y * b2.x),
+                                      0.25f * ((a2.x * a2.x + a2.y * a2.y) - (b2.x * b2.x + b2.y * b2.y)));
+        const float mq = fmaf(c2.x, c2.x, c2.y * c2.y);
+        const float sq = mq > 0.f ? exp2f(half_w * log2f(mq)) * inv_n2 : 0.f;
+        if (ky == 0) g = make_float2(0.f, 0.f);  // G[0,0] = 0
+        g = make_float2(g.x - c2.y * sq, g.y + c2.x * sq);
+      }
+      v[k2] = g;
+    }
+    dft<R2, +1>(v);
+#pragma unroll
+    for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(v[n2], twid[n2 * R1 + k1]);
+    if (dc_col) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) dcbuf[R2 * k1 + n2] = v[n2];
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) slab[(R2 * k1 + n2) * LS + lc] = v[n2];
+    }
+  }
+  __syncthreads();
+  // inverse pass A' -> H[y = n2 + R2 n1][kx]
+  float2* hw = W.h + s * N * (N / 2);
+#pragma unroll
+  for (int i = 0; i < (TAh + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if (TAh % T != 0 && task >= TAh) break;
+    const int n2 = task / CB, lc = task % CB;
+    const bool dc_col = (cb == 0 && lc == 0);
+    float2 v[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = dc_col ? dcbuf[n2 + R2 * k1] : slab[(n2 + R2 * k1) * LS + lc];
+    dft<R1, +1>(v);
+    const int kx = CB * cb + lc;  // 0 for the packed (DC, Nyquist) column
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) hw[(n2 + R2 * n1) * (N / 2) + kx] = v[n1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: inverse row transforms of row pairs (y, y + N/2), block argmax
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, const StreamWork W) {
+  using G = StreamGeom<N>;
+  constexpr int R1 = G::R1, R2 = G::R2, PB = G::PB, RS = G::RS, T = G::T;
+  const long long s = blockIdx.x / G::NB3;
+  const int pb = blockIdx.x % G::NB3;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (stat_status(W.stats[s]) != SWIFT_WIN_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* slab = reinterpret_cast<float2*>(smem_raw);  // [PB][RS]
+  float2* twid = slab + PB * RS;
+  __shared__ unsigned long long wkey[T / 32];
+  __shared__ double wsum[T / 32][2];
+  for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
+  // assemble packed rows P = H[y1] + i H[y2] with Hermitian completion
+  const float2* hw = W.h + s * N * (N / 2);
+  {
+    constexpr int K = PB * (N / 2) / T;
+    float2 h1[K], h2[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int e = tid + i * T;
+      const int p = e / (N / 2), kx = e % (N / 2);
+      const int y1 = pb * PB + p, y2 = y1 + N / 2;
+      h1[i] = __ldcs(hw + y1 * (N / 2) + kx);
+      h2[i] = __ldcs(hw + y2 * (N / 2) + kx);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int e = tid + i * T;
+      const int p = e / (N / 2), kx = e % (N / 2);
+      float2* row = slab + p * RS;
+      if (kx == 0) {
+        row[G::phys(0)] = make_float2(h1[i].x, h2[i].x);
+        row[G::phys(N / 2)] = make_float2(h1[i].y, h2[i].y);
+      } else {
+        row[G::phys(kx)] = make_float2(h1[i].x - h2[i].y, h1[i].y + h2[i].x);
+        row[G::phys(N - kx)] = make_float2(h1[i].x + h2[i].y, h2[i].x - h1[i].y);
+      }
+    }
+  }
+  __syncthreads();
+  constexpr int TA = PB * R2, TB = PB * R1;
+#pragma unroll
+  for (int i = 0; i < (TA + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if (TA % T != 0 && task >= TA) break;
+    const int p = task / R2, j = task % R2;
+    float2* row = slab + p * RS;
+    float2 v[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) v[m] = row[G::phys(j + R2 * m)];
+    dft<R1, +1>(v);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) row[G::phys(j + R2 * q)] = v[q];
+  }
+  __syncthreads();
+  float* surf = reinterpret_cast<float*>(W.zr + s * N * N);  // [N][N] response
+  unsigned long long best = 0ull;
+  float s1 = 0.f, s2 = 0.f;  // sums of s and s^2 over every pixel of the block
+#pragma unroll
+  for (int i = 0; i < (TB + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if (TB % T != 0 && task >= TB) break;
+    const int p = task / R1, k1 = task % R1;
+    const float2* row = slab + p * RS;
+    float2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      const float2 x = row[G::phys(R2 * k1 + n2)];
+      v[n2] = n2 == 0 ? x : cmulc(x, twid[n2 * R1 + k1]);
+    }
+    dft<R2, +1>(v);
+    const int y1 = pb * PB + p, y2 = y1 + N / 2;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int x = k1 + R1 * k2;
+      surf[y1 * N + x] = v[k2].x;
+      surf[y2 * N + x] = v[k2].y;
+      s1 += v[k2].x + v[k2].y;
+      s2 = fmaf(v[k2].x, v[k2].x, fmaf(v[k2].y, v[k2].y, s2));
+      const unsigned long long ka = argmax_key(v[k2].x, static_cast<uint32_t>(y1 * N + x));
+      const unsigned long long kb = argmax_key(v[k2].y, static_cast<uint32_t>(y2 * N + x));
+      best = ka > best ? ka : best;
+      best = kb > best ? kb : best;
+    }
+  }
+  best = warp_max_u64(best);
+  const double d1 = warp_sum_f64(static_cast<double>(s1)), d2 = warp_sum_f64(static_cast<double>(s2));
+  if (lane == 0) {
+    wkey[warp] = best;
+    wsum[warp][0] = d1;
+    wsum[warp][1] = d2;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long k = warp_max_u64(lane < T / 32 ? wkey[lane] : 0ull);
+    const double t1 = warp_sum_f64(lane < T / 32 ? wsum[lane][0] : 0.0);
+    const double t2 = warp_sum_f64(lane < T / 32 ? wsum[lane][1] : 0.0);
+    if (lane == 0) {
+      unsigned long long* part = W.part + 3 * (s * G::NB3 + pb);
+      part[0] = k;
+      part[1] = static_cast<unsigned long long>(__double_as_longlong(t1));
+      part[2] = static_cast<unsigned long long>(__double_as_longlong(t2));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: peak, SNR, subpixel, result
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) stream_final_kernel(const MatchLaunch L, const StreamWork W) {
+  using G = StreamGeom<N>;
+  const long long s = blockIdx.x;
+  const long long b = W.b0 + s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int st = stat_status(W.stats[s]);
+  if (st == kStatusSkip) return;
+  swift_result* out = L.out + b;
+  if (st != SWIFT_WIN_OK) {
+    if (tid == 0) {
+      swift_result r = {0, 0, 0.f, 0.f, 0.f, 0.f, st, 0};
+      *out = r;
+    }
+    return;
+  }
+  // one warp per window: totals from the block partials of K3, minus the
+  // pixels inside the exclusion disc (read back from the response), in FP64
+  if (warp != 0) return;
+  unsigned long long gk = 0ull;
+  double ta = 0.0, tc = 0.0;
+#pragma unroll
+  for (int k = 0; k < G::NB3; ++k) {
+    const unsigned long long* part = W.part + 3 * (s * G::NB3 + k);
+    const unsigned long long v = part[0];
+    gk = v > gk ? v : gk;
+    ta += __longlong_as_double(static_cast<long long>(part[1]));
+    tc += __longlong_as_double(static_cast<long long>(part[2]));
+  }
+  const uint32_t pidx = key_index(gk);
+  const int py = static_cast<int>(pidx / N), px = static_cast<int>(pidx % N);
+  const float* surf = reinterpret_cast<const float*>(W.zr + s * N * N);
+  const int R = static_cast<int>(sqrtf(L.radius2)) + 1;
+  double da = 0.0, dc = 0.0, dn = 0.0;
+  for (int e = lane; e < (2 * R + 1) * (2 * R + 1); e += 32) {
+    const int dy = e / (2 * R + 1) - R, dx = e % (2 * R + 1) - R;
+    if (static_cast<float>(dy * dy + dx * dx) <= L.radius2) {
+      const double v = surf[((py + dy) & (N - 1)) * N + ((px + dx) & (N - 1))];
+      da += v;
+      dc += v * v;
+      dn += 1.0;
+    }
+  }
+  da = warp_sum_f64(da);
+  dc = warp_sum_f64(dc);
+  dn = warp_sum_f64(dn);
+  if (lane == 0) {
+    const double tn = static_cast<double>(N) * N - dn;
+    ta -= da;
+    tc -= dc;
+    const double mu = ta / tn;
+    const double var = tc / tn - mu * mu;
+    const double pk = static_cast<double>(key_value(gk));
+    double snr;
+    if (var > 0.0) {
+      snr = (pk - mu) / sqrt(var);
+    } else {
+      snr = pk > mu ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
+    }
+    auto parab = [](double sm, double s0, double sp) -> double {
+      const double den = sm - 2.0 * s0 + sp;
+      if (!(den < 0.0)) return 0.0;
+      const double d = 0.5 * (sm - sp) / den;
+      return d < -0.5 ? -0.5 : (d > 0.5 ? 0.5 : d);
+    };
+    const double fy = parab(surf[((py + N - 1) & (N - 1)) * N + px], pk, surf[((py + 1) & (N - 1)) * N + px]);
+    const double fx = parab(surf[py * N + ((px + N - 1) & (N - 1))], pk, surf[py * N + ((px + 1) & (N - 1))]);
+    const int dy = py < N / 2 ? py : py - N;
+    const int dx = px < N / 2 ? px : px - N;
+    swift_result r;
+    r.dy = dy;
+    r.dx = dx;
+    r.sy = static_cast<float>(dy + fy);
+    r.sx = static_cast<float>(dx + fx);
+    r.snr = static_cast<float>(snr);
+    r.peak = static_cast<float>(pk);
+    r.status = SWIFT_WIN_OK;
+    r.reserved = 0;
+    *out = r;
+  }
+}
+
+}  // namespace swift

@@ -201,3 +201,43 @@ def test_deterministic(sections):
     r1 = plan.match(T(a), T(b), T(ro), T(ro)).clone()
     r2 = plan.match(T(a), T(b), T(ro), T(ro))
     assert torch.equal(r1, r2)
+
+
+@pytest.mark.parametrize("n", [64, 256])
+def test_persistent_loop_many_windows(sections, n):
+    """Far more windows than resident clusters, with out-of-bounds windows
+    mixed into every cluster's chain of staged loads."""
+    a, b = sections
+    rng = np.random.default_rng(77 + n)
+    B = 1500 if n == 64 else 700
+    ro = synth.random_origins(B, 1024, 1024, n, seed=n)
+    mo = np.clip(ro + rng.integers(-6, 7, ro.shape), 0, 1024 - n).astype(np.int32)
+    bad = rng.choice(B, B // 10, replace=False)
+    mo[bad, 1] = 1024 - n + 1 + rng.integers(0, 40, len(bad))  # leaves the section
+    lv = swift.Level(n, 0.65, "hann", 1.0, 3.0)
+    g = run_sections(a, b, ro, mo, lv)
+    assert set(np.nonzero(g["status"] == swim.OUT_OF_BOUNDS)[0]) == set(bad)
+    assert (g["status"][np.setdiff1d(np.arange(B), bad)] == 0).all()
+    sample = rng.choice(np.setdiff1d(np.arange(B), bad), 24, replace=False)
+    olv = oracle_level(lv)
+    for i in sample:
+        o, tied = oracle_window(swim.gather(b, mo[i], n), swim.gather(a, ro[i], n), olv)
+        compare(g, i, o, tied, n, f"persistent n={n}")
+    # the same pair anywhere in the batch gives bit-identical results
+    ro2 = np.concatenate([ro[:1]] * 300)
+    mo2 = np.concatenate([mo[sample[:1]]] * 300)
+    ro2[:, :] = ro[sample[0]]
+    g2 = run_sections(a, b, ro2, mo2, lv)
+    for k in ("dy", "dx", "sy", "sx", "snr", "peak", "status"):
+        assert (g2[k] == g2[k][0]).all()
+        assert g2[k][0] == g[k][sample[0]]
+
+
+def test_unaligned_section_width_uses_direct_loads(sections):
+    a, b = sections
+    n = 128
+    aw, bw = np.ascontiguousarray(a[:, :1001]), np.ascontiguousarray(b[:, :1001])  # width % 16 != 0
+    ro = synth.random_origins(20, 1024, 1001, n, seed=5)
+    lv = swift.Level(n, 0.65)
+    g = run_sections(aw, bw, ro, ro, lv)
+    check_sections(aw, bw, ro, ro, lv, g, "width 1001")
