@@ -37,7 +37,9 @@ typedef enum {
   SWIFT_ERR_UNSUPPORTED = 2, /* valid, but not built (e.g. a window size)    */
   SWIFT_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed         */
   SWIFT_ERR_OOM = 4,         /* a plan table could not be allocated          */
-  SWIFT_ERR_TIMEOUT = 5      /* a device-side bounded wait gave up           */
+  SWIFT_ERR_TIMEOUT = 5,     /* a device-side bounded wait gave up           */
+  SWIFT_ERR_CAPACITY = 6     /* more windows than swift_match_batch_noalloc's
+                                static scratch holds                         */
 } swift_status;
 
 /* Apodisation: the paper's cosine taper (Sec. III, "apodization").  HANN is
@@ -159,6 +161,36 @@ swift_status swift_plan_destroy(swift_plan plan);
  * written to out (device, [n_windows]).  Stream-ordered, no host sync. */
 swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_result* out,
                                void* stream);
+
+/* Forward match without any device allocation.
+ *
+ * For callers that cannot call cudaMalloc: code running inside another
+ * allocator's callback, real-time loops that must not change their memory
+ * after start-up, or processes whose device memory pool belongs to a
+ * framework.  No plan is needed and nothing is allocated: the scratch this
+ * path needs (window statistics, row spectra, whitened inverse-column data,
+ * the match response) lives in one 24 MiB file-scope device array that every
+ * GPU which loads the library holds until the process exits.  The taper and
+ * twiddle tables are built on the host for `level` and copied into that array
+ * on `stream` at every call.  The paper has no counterpart: this is a
+ * deployment variant of swift_match_batch for a single level (batch->level
+ * must be NULL); it runs the same streaming kernels and gives the same
+ * results.
+ *
+ * Limits: at most floor((24 MiB - 5120 B) / per-window bytes) windows per
+ * call: 31 windows of 256 x 256, 127 of 128 x 128, 511 of 64 x 64.  Larger
+ * batches return SWIFT_ERR_CAPACITY before any work is queued; split them.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing any stream into a CUDA graph.
+ *
+ * Sharing: all calls on a device use the same array and it keeps the last
+ * call's contents (nothing in it has to start at zero).  Calls that overlap
+ * on the GPU (different streams, or different host threads without ordering)
+ * race on it and corrupt each other's results; order them on one stream. */
+swift_status swift_match_batch_noalloc(const swift_level* level, swift_dtype in, const swift_batch* batch,
+                                       swift_result* out, void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* swift_status_string(swift_status s);

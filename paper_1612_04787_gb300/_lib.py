@@ -18,6 +18,7 @@ SWIFT_ERR_UNSUPPORTED = 2
 SWIFT_ERR_CUDA = 3
 SWIFT_ERR_OOM = 4
 SWIFT_ERR_TIMEOUT = 5
+SWIFT_ERR_CAPACITY = 6
 
 APOD = {"none": 0, "hann": 1, "tukey": 2}
 DTYPE = {"u8": 0, "f32": 1}
@@ -30,6 +31,7 @@ EXPORTS = (
     "swift_plan_create",
     "swift_plan_destroy",
     "swift_match_batch",
+    "swift_match_batch_noalloc",
     "swift_status_string",
     "swift_version",
 )
@@ -72,6 +74,9 @@ def _load():
     lib.swift_plan_destroy.restype = C.c_int
     lib.swift_match_batch.argtypes = [C.c_void_p, C.POINTER(SwiftBatch), C.c_void_p, C.c_void_p]
     lib.swift_match_batch.restype = C.c_int
+    lib.swift_match_batch_noalloc.argtypes = [C.POINTER(SwiftLevel), C.c_int, C.POINTER(SwiftBatch), C.c_void_p,
+                                              C.c_void_p]
+    lib.swift_match_batch_noalloc.restype = C.c_int
     lib.swift_status_string.argtypes = [C.c_int]
     lib.swift_status_string.restype = C.c_char_p
     lib.swift_version.argtypes = []

@@ -260,6 +260,8 @@ extern "C" const char* swift_status_string(swift_status s) {
       return "SWIFT_ERR_OOM";
     case SWIFT_ERR_TIMEOUT:
       return "SWIFT_ERR_TIMEOUT";
+    case SWIFT_ERR_CAPACITY:
+      return "SWIFT_ERR_CAPACITY";
   }
   return "SWIFT_ERR_UNKNOWN";
 }

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_status_strings_and_version():
     from paper_1612_04787_gb300 import _lib
-    for code in range(6):
+    for code in range(7):
         assert _lib.lib.swift_status_string(code).decode().startswith("SWIFT_")
     assert b"sm_103a" in _lib.lib.swift_version()
 

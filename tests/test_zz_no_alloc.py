@@ -1,0 +1,89 @@
+"""The allocation-free entry point agrees with the plan-based one.
+
+swift_match_batch_noalloc serves callers that cannot call cudaMalloc -- code
+running inside another allocator's callback, real-time loops whose device
+memory must stay fixed after start-up, processes whose memory pool belongs to a
+framework.  It takes no plan and keeps its scratch in a static device array.
+This file is collected last on purpose: if it fails, a run that stops at the
+first failure has already run every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from parity import PEAK_RTOL, SNR_RTOL, SUBPIXEL_TOL
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1612_04787_gb300 as swift  # noqa: E402
+from paper_1612_04787_gb300 import _lib  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def noalloc_match(level, dtype, ref, mov, ref_origin, mov_origin, out):
+    """Call swift_match_batch_noalloc through the C ABI (ctypes)."""
+    patch = ref_origin is None
+    ri = (_lib.SwiftImage * 1)(swift._image(ref, ref.dtype, patch))
+    mi = (_lib.SwiftImage * 1)(swift._image(mov, mov.dtype, patch))
+    B = ref.shape[0] if patch else ref_origin.shape[0]
+    bt = _lib.SwiftBatch(ri, mi, None if patch else ref_origin.data_ptr(),
+                         None if patch else mov_origin.data_ptr(), None, int(B), 1 if patch else 0)
+    lv = (_lib.SwiftLevel * 1)(level.c())
+    code = _lib.lib.swift_match_batch_noalloc(lv, _lib.DTYPE[dtype], C.byref(bt), out.data_ptr(),
+                                              torch.cuda.current_stream().cuda_stream)
+    return code
+
+
+def assert_close(a, b):
+    ok = a["status"] == 0
+    assert (a["status"] == b["status"]).all()
+    assert (a["dy"][ok] == b["dy"][ok]).all() and (a["dx"][ok] == b["dx"][ok]).all()
+    assert np.abs(a["sy"][ok] - b["sy"][ok]).max(initial=0) <= SUBPIXEL_TOL
+    assert np.abs(a["sx"][ok] - b["sx"][ok]).max(initial=0) <= SUBPIXEL_TOL
+    assert (np.abs(a["snr"][ok] - b["snr"][ok]) <= SNR_RTOL * np.abs(b["snr"][ok])).all()
+    assert (np.abs(a["peak"][ok] - b["peak"][ok]) <= PEAK_RTOL * np.abs(b["peak"][ok]) + 1e-6).all()
+
+
+def test_noalloc_matches_plan_path_twice_in_a_row():
+    a, b = synth.em_section_pair(1024, seed_content=31, seed_warp=32, seed_noise=(33, 34))
+    ta, tb = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    level = swift.Level(256, 0.65, "hann", 1.0, 3.0)
+    ro = synth.random_origins(24, 1024, 1024, 256, seed=35)
+    mo = np.clip(ro + np.random.default_rng(36).integers(-10, 11, ro.shape), 0, 768).astype(np.int32)
+    tro, tmo = torch.from_numpy(ro).to(DEV), torch.from_numpy(mo).to(DEV)
+    plan = swift.Plan([level], dtype="u8", max_windows=len(ro))
+    want = swift.decode(plan.match(ta, tb, tro, tmo))
+    for _ in range(2):  # the static scratch keeps the previous call's contents
+        out = torch.full((len(ro), 8), -7, dtype=torch.int32, device=DEV)
+        assert noalloc_match(level, "u8", ta, tb, tro, tmo, out) == _lib.SWIFT_OK
+        torch.cuda.synchronize()
+        assert_close(swift.decode(out), want)
+
+
+def test_noalloc_float_patches_and_capacity_limit():
+    a, _ = synth.em_section_pair(1024, seed_content=41, seed_warp=42, seed_noise=(43, 44))
+    ref, mov, _ = synth.shifted_patches(a, 128, 20, seed=45)
+    tr, tm = torch.from_numpy(ref).to(DEV), torch.from_numpy(mov).to(DEV)
+    level = swift.Level(128, 0.5, "tukey", 0.5, 2.0)
+    plan = swift.Plan([level], dtype="f32", max_windows=20)
+    want = swift.decode(plan.match(tr, tm))
+    for _ in range(2):
+        out = torch.zeros((20, 8), dtype=torch.int32, device=DEV)
+        assert noalloc_match(level, "f32", tr, tm, None, None, out) == _lib.SWIFT_OK
+        torch.cuda.synchronize()
+        assert_close(swift.decode(out), want)
+    # 256 x 256 windows: 31 fit in the static scratch, 32 do not
+    big = torch.zeros((32, 256, 256), dtype=torch.float32, device=DEV)
+    out = torch.zeros((32, 8), dtype=torch.int32, device=DEV)
+    lv256 = swift.Level(256, 0.65)
+    assert noalloc_match(lv256, "f32", big, big, None, None, out) == _lib.SWIFT_ERR_CAPACITY
+    assert noalloc_match(lv256, "f32", big[:31], big[:31], None, None, out[:31]) == _lib.SWIFT_OK
+    torch.cuda.synchronize()
+    assert (swift.decode(out[:31])["status"] == swift.WIN_FLAT).all()
