@@ -348,3 +348,103 @@ def match_batch(ref_sections, mov_sections, ref_origins, mov_origins, levels,
 def match_patches(ref, mov, level: Level):
     """Match [B, n, n] patch pairs (no gather)."""
     return [match_pair(mov[b], ref[b], level) for b in range(len(ref))]
+
+
+# --------------------------------------------------------------------------- #
+# adjoint (gradients of peak height and SNR)
+# --------------------------------------------------------------------------- #
+def bilinear_grad(section: np.ndarray, Y: np.ndarray, X: np.ndarray):
+    """d(bilinear sample)/dY and d/dX at (Y, X) (inside the section)."""
+    h, w = section.shape
+    y0 = np.minimum(np.floor(Y).astype(np.int64), h - 2)
+    x0 = np.minimum(np.floor(X).astype(np.int64), w - 2)
+    fy, fx = Y - y0, X - x0
+    S = section.astype(np.float64)
+    s00, s01, s10, s11 = S[y0, x0], S[y0, x0 + 1], S[y0 + 1, x0], S[y0 + 1, x0 + 1]
+    dY = (1 - fx) * (s10 - s00) + fx * (s11 - s01)
+    dX = (1 - fy) * (s01 - s00) + fy * (s11 - s10)
+    return dY, dX
+
+
+def match_backward(mov_section, origin, theta, ref_w, level: Level, grad_peak: float,
+                   grad_snr: float):
+    """Gradient of L = grad_peak * peak + grad_snr * snr of one window pair.
+
+    The moving window is the section resampled under ``theta`` (see
+    ``resample``); the reference window is fixed.  The peak index and hence
+    the background set are held fixed (the argmax has no derivative).  Returns
+    (forward result dict, dL/dtheta [6], dL/dw).
+
+    Chain, in the order of the forward step it undoes:
+      dL/ds      peak term: delta at the peak; SNR term:
+                 (delta_peak - [bg]/n_bg - snr [bg] (s - mu_bg)/(n_bg sigma_bg)) / sigma_bg
+      dL/dG      = DFT2(dL/ds)          (s = Re IDFT2(G); complex gradient
+                                          convention g = dL/dRe + i dL/dIm)
+      dL/dC      = e^{i phi} rho^-w [(1 - w) Re(u) - i Im(u)] / n^2 with
+                   u = conj(dL/dG) e^{i phi}, C = rho e^{i phi}
+      dL/dw      = -sum_k ln(rho_k) Re(conj(dL/dG_k) G_k)
+      dL/dM      = dL/dC * R            (C = M conj(R))
+      dL/dm'     = Re( n^2 IDFT2(dL/dM) ) (M = DFT2(m'), m' real)
+      dL/dm      = A dL/dm' - A sum(A dL/dm') / sum(A)   (m' = A (m - mu_A))
+      dL/dtheta  = sum_ij dL/dm_ij d(bilinear)/d(Y, X) d(Y, X)/dtheta
+    """
+    n = level.n
+    theta = np.asarray(theta, dtype=np.float64)
+    Y, X = affine_sample_points(origin, n, theta)
+    mov_w = bilinear(mov_section, Y, X)
+    if mov_w is None:
+        raise ValueError("resampled window leaves the section")
+    A = taper_2d(n, level.apod, level.tukey_alpha)
+    mp = apodise(mov_w, A)
+    rp = apodise(np.asarray(ref_w, dtype=np.float64), A)
+    M = dft2(mp)
+    R = dft2(rp)
+    C = M * np.conj(R)
+    w = level.whiten_exponent
+    G = whiten(C, w) / (n * n)
+    s = (idft2(G) * (n * n)).real  # G already carries 1/n^2
+    py, px = peak_index(s)
+    z, mu, sd = snr(s, py, px, level.snr_exclusion_radius)
+    bg = background_mask(n, py, px, level.snr_exclusion_radius)
+    nbg = float(bg.sum())
+    peak = float(s[py, px])
+    # dL/ds
+    gs = np.zeros((n, n))
+    gs[py, px] += grad_peak + grad_snr / sd
+    gs[bg] += grad_snr * (-1.0 / (nbg * sd) - z * (s[bg] - mu) / (nbg * sd * sd))
+    # dL/dG (complex-gradient convention)
+    gG = dft2(gs)
+    rho = np.abs(C)
+    valid = rho > 0
+    valid[0, 0] = False
+    e = np.zeros_like(C)
+    e[valid] = C[valid] / rho[valid]
+    u = np.conj(gG) * e
+    gC = np.zeros_like(C)
+    gC[valid] = (e[valid] * rho[valid] ** (-w) / (n * n)
+                 * ((1.0 - w) * u[valid].real - 1j * u[valid].imag))
+    gw = -float(np.sum(np.log(rho[valid]) * (np.conj(gG[valid]) * G[valid]).real))
+    gM = gC * R
+    gmp = (idft2(gM) * (n * n)).real
+    gm = A * gmp - A * float((A * gmp).sum()) / float(A.sum())
+    dY, dX = bilinear_grad(mov_section, Y, X)
+    c = n / 2.0
+    ii, jj = np.meshgrid(np.arange(n, dtype=np.float64) - c, np.arange(n, dtype=np.float64) - c,
+                         indexing="ij")
+    gy, gx = gm * dY, gm * dX
+    gtheta = np.array([(gy * ii).sum(), (gy * jj).sum(), gy.sum(),
+                       (gx * ii).sum(), (gx * jj).sum(), gx.sum()])
+    fwd = dict(dy=signed_shift(py, n), dx=signed_shift(px, n), snr=z, peak=peak, status=OK)
+    return fwd, gtheta, gw
+
+
+def affine_objective(mov_section, origin, theta, ref_w, level: Level, grad_peak: float,
+                     grad_snr: float, peak_at=None):
+    """L = grad_peak * peak + grad_snr * snr with the peak optionally held at
+    ``peak_at`` = (py, px) (the envelope the adjoint differentiates)."""
+    n = level.n
+    mov_w = resample(mov_section, origin, n, theta)
+    s = match_surface(mov_w, ref_w, level)
+    py, px = peak_at if peak_at is not None else peak_index(s)
+    z, _, _ = snr(s, py, px, level.snr_exclusion_radius)
+    return grad_peak * float(s[py, px]) + grad_snr * z
