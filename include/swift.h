@@ -110,7 +110,16 @@ typedef struct {
  *   n_windows    B >= 0 (0 is a no-op)
  *   patch_mode   0: windows are cut from images at the origins;
  *                1: window b of level l is the n x n patch starting at
- *                   data + b * stride (pitch = n) of ref[l] / mov[l]         */
+ *                   data + b * stride (pitch = n) of ref[l] / mov[l]
+ *   affine       device float [B][6] or NULL.  When set (section mode only),
+ *                moving-window pixel (i, j) is the bilinear sample of mov[l]
+ *                at origin + c + [[a_yy, a_yx], [a_xy, a_xx]] (i - c, j - c)
+ *                + (t_y, t_x), c = n/2, for theta = (a_yy, a_yx, t_y, a_xy,
+ *                a_xx, t_x) -- a locally affine warp of the window (Sec. III,
+ *                mir's affine triangles).  A window whose warped corners
+ *                leave [0, h-1] x [0, w-1] is OUT_OF_BOUNDS.  The first call
+ *                with warps (or the first backward) allocates the plan's
+ *                extra workspace; make it before capturing the stream.      */
 typedef struct {
   const swift_image* ref;
   const swift_image* mov;
@@ -119,6 +128,7 @@ typedef struct {
   const int32_t* level;
   int64_t n_windows;
   int32_t patch_mode;
+  const float* affine;
 } swift_batch;
 
 /* Result of one window pair (32 bytes).
@@ -191,6 +201,25 @@ swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_
  * race on it and corrupt each other's results; order them on one stream. */
 swift_status swift_match_batch_noalloc(const swift_level* level, swift_dtype in, const swift_batch* batch,
                                        swift_result* out, void* stream);
+
+/* Backward of the match: gradients of
+ *     L = sum_b grad_peak[b] * peak_b + grad_snr[b] * snr_b
+ * with respect to the affine warp of every moving window (batch->affine, or
+ * the identity warp when NULL) and to each level's whitening exponent.  The
+ * peak index of each window (and with it the SNR background set) is held
+ * fixed: the argmax has no derivative.  The forward is recomputed from the
+ * inputs (no state is kept between calls).  Windows whose status is not OK
+ * get zero gradients.
+ *   grad_peak, grad_snr   device float [B]
+ *   grad_affine           device float [B][6], same order as the warp
+ *   grad_w                device float [n_levels] (summed over the batch)
+ * Section mode only.  Stream-ordered; may allocate the plan's extra workspace
+ * on its first call. */
+swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, const float* grad_peak,
+                                  const float* grad_snr, float* grad_affine, float* grad_w, void* stream);
+
+/* Set the whitening exponent of one level for later calls (w in [0, 1]). */
+swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w);
 
 /* Human-readable name of a status code (static string). */
 const char* swift_status_string(swift_status s);

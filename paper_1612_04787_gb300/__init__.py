@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import (APOD, DTYPE, PRECISION, SwiftBatch, SwiftImage, SwiftLevel, SwiftError,  # noqa: F401
                    WIN_FLAT, WIN_NONFINITE, WIN_OK, WIN_OUT_OF_BOUNDS, check, lib)
 
-__all__ = ["Level", "Plan", "decode", "SwiftError", "version", "WIN_OK", "WIN_OUT_OF_BOUNDS",
+__all__ = ["Level", "Plan", "decode", "SwiftError", "version", "match_warped", "WIN_OK", "WIN_OUT_OF_BOUNDS",
            "WIN_FLAT", "WIN_NONFINITE"]
 
 
@@ -100,15 +100,12 @@ class Plan:
     def handle(self) -> int:
         return self._h.value
 
-    def match(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None):
-        """Forward match; returns ``out`` ([B, 8] int32 device tensor of results).
+    def set_whitening(self, level: int, w: float):
+        """Whitening exponent of one level for later calls."""
+        check(lib.swift_plan_set_whitening(self._h, int(level), float(w)), "swift_plan_set_whitening")
+        self.levels[level].whiten_exponent = float(w)
 
-        Section mode: ``ref`` / ``mov`` are [H, W] uint8/float32 images (``ref``
-        may be [K, H, W]: the reference window is then the mean of K
-        sections) or lists with one image per level, and the origins are
-        int32 [B, 2] (y, x) device tensors.  Patch mode (no origins): ``ref``
-        and ``mov`` are [B, n, n] stacks.
-        """
+    def _batch(self, ref, mov, ref_origin, mov_origin, level, affine):
         patch = ref_origin is None and mov_origin is None
         refs = ref if isinstance(ref, (list, tuple)) else [ref]
         movs = mov if isinstance(mov, (list, tuple)) else [mov]
@@ -126,10 +123,12 @@ class Plan:
         if level is not None:
             if level.dtype != torch.int32 or not level.is_cuda or not level.is_contiguous() or level.numel() != B:
                 raise ValueError("level must be a contiguous int32 [B] CUDA tensor")
-        if out is None:
-            out = torch.empty((B, 8), dtype=torch.int32, device=refs[0].device)
-        elif out.dtype != torch.int32 or out.shape != (B, 8) or not out.is_contiguous():
-            raise ValueError("out must be a contiguous int32 [B, 8] tensor")
+        if affine is not None:
+            if patch:
+                raise ValueError("affine warps need section mode (origins)")
+            if affine.dtype != torch.float32 or not affine.is_cuda or not affine.is_contiguous() \
+                    or tuple(affine.shape) != (B, 6):
+                raise ValueError("affine must be a contiguous float32 [B, 6] CUDA tensor")
         nl = len(refs)
         ri = (SwiftImage * nl)(*[_image(t, self.torch_dtype, patch) for t in refs])
         mi = (SwiftImage * nl)(*[_image(t, self.torch_dtype, patch) for t in movs])
@@ -137,10 +136,85 @@ class Plan:
                         None if patch else ref_origin.data_ptr(),
                         None if patch else mov_origin.data_ptr(),
                         None if level is None else level.data_ptr(),
-                        int(B), 1 if patch else 0)
+                        int(B), 1 if patch else 0,
+                        None if affine is None else affine.data_ptr())
+        return bt, (ri, mi), B, refs[0].device
+
+    def backward(self, ref, mov, ref_origin, mov_origin, grad_peak, grad_snr, affine=None, level=None,
+                 stream=None):
+        """Gradients of sum(grad_peak * peak + grad_snr * snr) with respect to
+        the affine warps ([B, 6]) and the levels' whitening exponents
+        ([n_levels]); the peak positions are held fixed."""
+        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, affine)
+        gp = grad_peak.to(device=dev, dtype=torch.float32).contiguous()
+        gs = grad_snr.to(device=dev, dtype=torch.float32).contiguous()
+        if gp.numel() != B or gs.numel() != B:
+            raise ValueError("grad_peak and grad_snr need one value per window")
+        g_aff = torch.zeros((B, 6), dtype=torch.float32, device=dev)
+        g_w = torch.zeros((len(self.levels),), dtype=torch.float32, device=dev)
+        check(lib.swift_match_backward(self._h, C.byref(bt), gp.data_ptr(), gs.data_ptr(), g_aff.data_ptr(),
+                                       g_w.data_ptr(), _stream_ptr(stream)), "swift_match_backward")
+        return g_aff, g_w
+
+    def match(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None, affine=None):
+        """Forward match; returns ``out`` ([B, 8] int32 device tensor of results).
+
+        Section mode: ``ref`` / ``mov`` are [H, W] uint8/float32 images (``ref``
+        may be [K, H, W]: the reference window is then the mean of K
+        sections) or lists with one image per level, and the origins are
+        int32 [B, 2] (y, x) device tensors.  Patch mode (no origins): ``ref``
+        and ``mov`` are [B, n, n] stacks.  ``affine`` ([B, 6] float32, section
+        mode) resamples each moving window bilinearly under its warp.
+        """
+        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, affine)
+        if out is None:
+            out = torch.empty((B, 8), dtype=torch.int32, device=dev)
+        elif out.dtype != torch.int32 or out.shape != (B, 8) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous int32 [B, 8] tensor")
         check(lib.swift_match_batch(self._h, C.byref(bt), out.data_ptr(), _stream_ptr(stream)),
               "swift_match_batch")
         return out
+
+
+class _MatchFn(torch.autograd.Function):
+    """(affine [B, 6], w [n_levels]) -> (peak [B], snr [B]); backward through
+    the library's adjoint kernels (peak positions held fixed)."""
+
+    @staticmethod
+    def forward(ctx, affine, w, plan, ref, mov, ref_origin, mov_origin, level):
+        for l, wl in enumerate(w.detach().cpu().tolist()):
+            plan.set_whitening(l, wl)
+        res = plan.match(ref, mov, ref_origin, mov_origin, level=level, affine=affine.detach().contiguous())
+        f = res.view(torch.float32)
+        peak = f[:, 5].clone()
+        snr = f[:, 4].clone()
+        ctx.plan = plan
+        ctx.w_device = w.device
+        ctx.args = (ref, mov, ref_origin, mov_origin, level)
+        ctx.save_for_backward(affine)
+        ctx.mark_non_differentiable(res)
+        return peak, snr, res
+
+    @staticmethod
+    def backward(ctx, grad_peak, grad_snr, _grad_res):
+        (affine,) = ctx.saved_tensors
+        ref, mov, ro, mo, level = ctx.args
+        B = affine.shape[0]
+        gp = grad_peak if grad_peak is not None else torch.zeros(B, device=affine.device)
+        gs = grad_snr if grad_snr is not None else torch.zeros(B, device=affine.device)
+        g_aff, g_w = ctx.plan.backward(ref, mov, ro, mo, gp, gs, affine=affine.detach().contiguous(), level=level)
+        return g_aff, g_w.to(ctx.w_device), None, None, None, None, None, None
+
+
+def match_warped(plan: Plan, ref, mov, ref_origin, mov_origin, affine, w, level=None):
+    """Differentiable match of affinely warped moving windows.
+
+    ``affine``: [B, 6] float32 CUDA tensor (a_yy, a_yx, t_y, a_xy, a_xx, t_x);
+    ``w``: [n_levels] float32 tensor of whitening exponents.  Returns
+    (peak [B], snr [B], results [B, 8]); gradients flow to ``affine`` and
+    ``w`` through the library's backward kernels.
+    """
+    return _MatchFn.apply(affine, w, plan, ref, mov, ref_origin, mov_origin, level)
 
 
 def decode(res) -> dict:

@@ -32,6 +32,8 @@ EXPORTS = (
     "swift_plan_destroy",
     "swift_match_batch",
     "swift_match_batch_noalloc",
+    "swift_match_backward",
+    "swift_plan_set_whitening",
     "swift_status_string",
     "swift_version",
 )
@@ -50,7 +52,7 @@ class SwiftImage(C.Structure):
 class SwiftBatch(C.Structure):
     _fields_ = [("ref", C.POINTER(SwiftImage)), ("mov", C.POINTER(SwiftImage)),
                 ("ref_origin", C.c_void_p), ("mov_origin", C.c_void_p), ("level", C.c_void_p),
-                ("n_windows", C.c_int64), ("patch_mode", C.c_int32)]
+                ("n_windows", C.c_int64), ("patch_mode", C.c_int32), ("affine", C.c_void_p)]
 
 
 class SwiftResult(C.Structure):
@@ -77,6 +79,11 @@ def _load():
     lib.swift_match_batch_noalloc.argtypes = [C.POINTER(SwiftLevel), C.c_int, C.POINTER(SwiftBatch), C.c_void_p,
                                               C.c_void_p]
     lib.swift_match_batch_noalloc.restype = C.c_int
+    lib.swift_match_backward.argtypes = [C.c_void_p, C.POINTER(SwiftBatch), C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]
+    lib.swift_match_backward.restype = C.c_int
+    lib.swift_plan_set_whitening.argtypes = [C.c_void_p, C.c_int32, C.c_float]
+    lib.swift_plan_set_whitening.restype = C.c_int
     lib.swift_status_string.argtypes = [C.c_int]
     lib.swift_status_string.restype = C.c_char_p
     lib.swift_version.argtypes = []

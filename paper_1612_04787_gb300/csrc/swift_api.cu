@@ -56,11 +56,17 @@ struct swift_plan_s {
   int stream_level[kMaxLevels] = {};
   void* work = nullptr;
   long long work_windows = 0;  // capacity (windows of the largest streamed size)
+  // affine-warp forward and backward: allocated on first use
+  void* bwork = nullptr;
+  long long bwork_windows = 0;
+  double* gw_acc = nullptr;  // [kMaxLevels] accumulated dL/dw
 };
 
 namespace {
 // windows per slice of the streaming path (bounds its workspace)
 constexpr long long kStreamSlice = 2048;
+// windows per slice of the affine / backward path
+constexpr long long kBackSlice = 1024;
 // default forward schedule: 256 x 256 and 128 x 128 windows stream their
 // intermediates through the workspace; 64 x 64 windows use the fused kernel
 bool default_stream(int n) { return n >= 128; }
@@ -76,6 +82,8 @@ static swift_status release(swift_plan p) {
   for (int i = 0; i < 3; ++i)
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
   if (p->work) cudaFree(p->work);
+  if (p->bwork) cudaFree(p->bwork);
+  if (p->gw_acc) cudaFree(p->gw_acc);
   if (cur != p->device) cudaSetDevice(cur);
   delete p;
   return SWIFT_OK;
@@ -180,6 +188,9 @@ static bool image_ok(const swift_image& im, int n, int patch_mode, int64_t B) {
   return true;
 }
 
+static swift_status check_warp_batch(swift_plan plan, const swift_batch* batch);
+static swift_status warp_forward(swift_plan plan, const swift_batch* batch, swift_result* out, cudaStream_t st);
+
 extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_result* out,
                                           void* stream) {
   if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
@@ -199,6 +210,11 @@ extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* ba
   // report (and clear) an asynchronous failure left by earlier work
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (batch->affine) {
+    const swift_status e = check_warp_batch(plan, batch);
+    if (e != SWIFT_OK) return e;
+    return warp_forward(plan, batch, out, st);
+  }
   for (int l = 0; l < used_levels; ++l) {
     const swift_level& lv = plan->levels[l];
     const swift_image& ri = batch->ref[l];
@@ -243,6 +259,136 @@ extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* ba
     if (swift::launch_forward(lv.n, plan->dtype, bulk, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
   }
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  return SWIFT_OK;
+}
+
+// Launch description of level l (shared by the warp and backward paths).
+static swift::MatchLaunch level_launch(swift_plan plan, const swift_batch* batch, int l, swift_result* out) {
+  const swift_level& lv = plan->levels[l];
+  const swift_image& ri = batch->ref[l];
+  const swift_image& mi = batch->mov[l];
+  swift::MatchLaunch L;
+  L.ref = ri.data;
+  L.mov = mi.data;
+  L.ref_pitch = ri.pitch;
+  L.mov_pitch = mi.pitch;
+  L.ref_stride = ri.stride;
+  L.mov_stride = mi.stride;
+  L.ref_h = ri.height;
+  L.ref_w = ri.width;
+  L.mov_h = mi.height;
+  L.mov_w = mi.width;
+  L.ref_count = ri.count;
+  L.patch_mode = 0;
+  L.ref_origin = batch->ref_origin;
+  L.mov_origin = batch->mov_origin;
+  L.level_idx = batch->level;
+  L.level = l;
+  L.n_windows = batch->n_windows;
+  L.w = lv.whiten_exponent;
+  L.radius2 = static_cast<float>(floor(static_cast<double>(lv.snr_exclusion_radius) * lv.snr_exclusion_radius));
+  L.inv_sum_a = plan->inv_sum_a[l];
+  L.taper = plan->taper[l];
+  L.twiddle = plan->twiddle[size_slot(lv.n)];
+  L.out = out;
+  L.pre_status = nullptr;
+  return L;
+}
+
+// extra workspace of the warp / backward path, allocated on first use
+static swift_status ensure_bwork(swift_plan plan) {
+  if (plan->bwork) return SWIFT_OK;
+  size_t per = 0;
+  for (int l = 0; l < plan->n_levels; ++l) {
+    const size_t b = swift::back_bytes_per_window(plan->levels[l].n);
+    per = b > per ? b : per;
+  }
+  const long long cap = plan->max_windows < kBackSlice ? plan->max_windows : kBackSlice;
+  if (cudaMalloc(&plan->bwork, per * cap + 16 * 4096) != cudaSuccess) {
+    plan->bwork = nullptr;
+    cudaGetLastError();
+    return SWIFT_ERR_OOM;
+  }
+  if (cudaMalloc(&plan->gw_acc, sizeof(double) * kMaxLevels) != cudaSuccess) {
+    cudaFree(plan->bwork);
+    plan->bwork = nullptr;
+    plan->gw_acc = nullptr;
+    cudaGetLastError();
+    return SWIFT_ERR_OOM;
+  }
+  plan->bwork_windows = cap;
+  return SWIFT_OK;
+}
+
+// validation shared by the warp forward and the backward (section mode)
+static swift_status check_warp_batch(swift_plan plan, const swift_batch* batch) {
+  if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
+  const int64_t B = batch->n_windows;
+  if (B < 0 || B > plan->max_windows) return SWIFT_ERR_INVALID_ARG;
+  if (B == 0) return SWIFT_OK;
+  if (batch->patch_mode || !batch->ref || !batch->mov || !batch->ref_origin || !batch->mov_origin)
+    return SWIFT_ERR_INVALID_ARG;
+  const int used = batch->level ? plan->n_levels : 1;
+  for (int l = 0; l < used; ++l) {
+    if (!image_ok(batch->ref[l], plan->levels[l].n, 0, B) || !image_ok(batch->mov[l], plan->levels[l].n, 0, B))
+      return SWIFT_ERR_INVALID_ARG;
+    if (batch->mov[l].count != 1 || batch->mov[l].height < 2 || batch->mov[l].width < 2) return SWIFT_ERR_INVALID_ARG;
+  }
+  return SWIFT_OK;
+}
+
+static swift_status warp_forward(swift_plan plan, const swift_batch* batch, swift_result* out, cudaStream_t st) {
+  swift_status e = ensure_bwork(plan);
+  if (e != SWIFT_OK) return e;
+  const int used = batch->level ? plan->n_levels : 1;
+  const long long B = batch->n_windows;
+  for (int l = 0; l < used; ++l) {
+    const swift::MatchLaunch L = level_launch(plan, batch, l, out);
+    swift::BackLaunch K = {batch->affine, nullptr, nullptr, nullptr, nullptr};
+    for (long long b0 = 0; b0 < B; b0 += plan->bwork_windows) {
+      const long long cnt = (B - b0) < plan->bwork_windows ? (B - b0) : plan->bwork_windows;
+      const swift::BackWork BW = swift::back_carve(plan->bwork, plan->bwork_windows, plan->levels[l].n, cnt);
+      if (swift::launch_prepare(plan->levels[l].n, plan->dtype, L, K, BW, b0, st) != cudaSuccess ||
+          swift::launch_prepared_forward(plan->levels[l].n, L, BW, b0, st) != cudaSuccess)
+        return SWIFT_ERR_CUDA;
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, const float* grad_peak,
+                                             const float* grad_snr, float* grad_affine, float* grad_w,
+                                             void* stream) {
+  swift_status e = check_warp_batch(plan, batch);
+  if (e != SWIFT_OK) return e;
+  const long long B = batch->n_windows;
+  if (!grad_w) return SWIFT_ERR_INVALID_ARG;
+  if (B > 0 && (!grad_peak || !grad_snr || !grad_affine)) return SWIFT_ERR_INVALID_ARG;
+  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  if ((e = ensure_bwork(plan)) != SWIFT_OK) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(plan->gw_acc, 0, sizeof(double) * kMaxLevels, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+  const int used = batch->level ? plan->n_levels : 1;
+  for (int l = 0; l < used && B > 0; ++l) {
+    const swift::MatchLaunch L = level_launch(plan, batch, l, nullptr);
+    const swift::BackLaunch K = {batch->affine, grad_peak, grad_snr, grad_affine, plan->gw_acc + l};
+    for (long long b0 = 0; b0 < B; b0 += plan->bwork_windows) {
+      const long long cnt = (B - b0) < plan->bwork_windows ? (B - b0) : plan->bwork_windows;
+      const swift::BackWork BW = swift::back_carve(plan->bwork, plan->bwork_windows, plan->levels[l].n, cnt);
+      if (swift::launch_prepare(plan->levels[l].n, plan->dtype, L, K, BW, b0, st) != cudaSuccess ||
+          swift::launch_backward(plan->levels[l].n, plan->dtype, L, K, BW, b0, st) != cudaSuccess)
+        return SWIFT_ERR_CUDA;
+    }
+  }
+  if (swift::launch_wout(plan->gw_acc, grad_w, plan->n_levels, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w) {
+  if (!plan || level < 0 || level >= plan->n_levels || !(w >= 0.f && w <= 1.f)) return SWIFT_ERR_INVALID_ARG;
+  plan->levels[level].whiten_exponent = w;
   return SWIFT_OK;
 }
 

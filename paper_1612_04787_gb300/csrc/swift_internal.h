@@ -27,6 +27,7 @@ struct MatchLaunch {
   const float* taper;                // [n] 1D taper
   const float2* twiddle;             // [R2][R1] forward W_n^{j m}
   swift_result* out;                 // [B]
+  const int* pre_status = nullptr;   // [slice] status decided before the statistics (or null)
 };
 
 // Workspace of the streaming forward path for one slice of windows.
@@ -43,6 +44,46 @@ struct StreamWork {
 size_t stream_bytes_per_window(int n);
 StreamWork stream_carve(void* base, long long capacity, int n, long long b0, long long count);
 cudaError_t launch_stream(int n, swift_dtype dtype, const MatchLaunch& L, const StreamWork& W, cudaStream_t stream);
+
+// Extra workspace of the affine-warp forward and the backward pass (one slice).
+// The backward reuses the forward's H for the inverse-column output of dL/dM
+// and Zr (as float [n][n]) for dL/dm'.
+struct BackWork {
+  StreamWork fw;   // forward workspace
+  float* mp;       // [S][n][n] prepared moving windows (affine-resampled)
+  float* rp;       // [S][n][n] prepared reference windows (gathered / projected)
+  int* pre_status; // [S] bounds / level decided by the preparation kernel
+  float2* cr;      // [S][2][n][n/2+1] C = M conj(R) and R, kx in [0, n/2]
+  double* bst;     // [S][8] mu_bg, sigma_bg, snr, peak, py, px, status, n_bg
+  float2* gr;      // [S][n][n/2+1] row spectra of dL/ds
+  double* gwp;     // [S][blocks] partial dL/dw
+  double* gsum;    // [S][blocks] partial sum of A dL/dm'
+  double* gwin;    // [S] dL/dw of each window
+};
+
+struct BackLaunch {
+  const float* affine;     // [B][6] (a_yy, a_yx, t_y, a_xy, a_xx, t_x) or null (identity)
+  const float* grad_peak;  // [B]
+  const float* grad_snr;   // [B]
+  float* grad_affine;      // [B][6]
+  double* gw_acc;          // accumulated dL/dw of this level (device, one double)
+};
+
+// affine-warp forward and backward (swim_backward.cu)
+size_t back_bytes_per_window(int n);
+BackWork back_carve(void* base, long long capacity, int n, long long count);
+// prepare windows (resample / gather) for a slice [b0, b0 + count) of the batch
+cudaError_t launch_prepare(int n, swift_dtype dtype, const MatchLaunch& L, const BackLaunch& K, const BackWork& BW,
+                           long long b0, cudaStream_t stream);
+// forward on the prepared windows (results to L.out)
+cudaError_t launch_prepared_forward(int n, const MatchLaunch& L, const BackWork& BW, long long b0,
+                                    cudaStream_t stream);
+// backward on the prepared windows (accumulates into K.gw_acc, writes K.grad_affine)
+cudaError_t launch_backward(int n, swift_dtype dtype, const MatchLaunch& L, const BackLaunch& K, const BackWork& BW,
+                            long long b0, cudaStream_t stream);
+
+// float32 copy of the accumulated dL/dw of n levels
+cudaError_t launch_wout(const double* acc, float* out, int n, cudaStream_t stream);
 
 // forward launchers (one per window size), defined in swim_forward.cu
 // bulk: stage uint8 section rows with cp.async.bulk (needs 16-byte aligned

@@ -24,31 +24,6 @@ size_t blocks3(int n) {
 }
 
 template <int N, typename TIn>
-constexpr size_t rows_smem() {
-  using G = StreamGeom<N>;
-  return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * N + 2 * sizeof(TIn) * G::RB * N;
-}
-template <int N>
-constexpr size_t cols_smem() {
-  using G = StreamGeom<N>;
-  return sizeof(float2) * (N * (2 * G::CB + 8) + 2 * N);
-}
-template <int N>
-constexpr size_t irows_smem() {
-  using G = StreamGeom<N>;
-  return sizeof(float2) * (G::PB * G::RS + N);
-}
-
-// dynamic shared-memory opt-in, once per device and kernel
-template <typename K>
-cudaError_t smem_optin(K kern, size_t bytes, unsigned& done_mask, int dev) {
-  if (dev < 32 && (done_mask & (1u << dev))) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-  if (e == cudaSuccess && dev < 32) done_mask |= 1u << dev;
-  return e;
-}
-
-template <int N, typename TIn>
 cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st) {
   using G = StreamGeom<N>;
   const unsigned S = static_cast<unsigned>(W.count);

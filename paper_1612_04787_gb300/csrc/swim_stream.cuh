@@ -73,6 +73,10 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
   auto put = [&](int status, float mm, float mr) {
     if (tid == 0) W.stats[s] = make_float4(mm, mr, __int_as_float(status), 0.f);
   };
+  if (L.pre_status != nullptr && L.pre_status[s] != SWIFT_WIN_OK) {
+    put(L.pre_status[s], 0.f, 0.f);
+    return;
+  }
   if (L.level_idx != nullptr && __ldg(L.level_idx + b) != L.level) {
     put(kStatusSkip, 0.f, 0.f);
     return;
@@ -312,8 +316,11 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
 // ---------------------------------------------------------------------------
 // K2: column transforms, unpack, whitening, inverse column transforms
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(256) stream_cols_kernel(const MatchLaunch L, const StreamWork W) {
+// SAVE: also store C = M conj(R) and R for kx in [0, n/2] (all ky) to `cr`
+// ([2][n][n/2+1]) for the backward pass.
+template <int N, bool SAVE = false>
+__global__ void __launch_bounds__(256) stream_cols_kernel(const MatchLaunch L, const StreamWork W,
+                                                          float2* cr = nullptr) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, CB = G::CB, T = G::T;
   constexpr int LINES = 2 * CB;
@@ -395,11 +402,22 @@ __global__ void __launch_bounds__(256) stream_cols_kernel(const MatchLaunch L, c
       const float mag2 = fmaf(c.x, c.x, c.y * c.y);
       const float sc = mag2 > 0.f ? exp2f(half_w * log2f(mag2)) * inv_n2 : 0.f;
       float2 g = make_float2(c.x * sc, c.y * sc);
+      if constexpr (SAVE) {
+        // R = (A - conj(B)) / 2i
+        const size_t o = (static_cast<size_t>(s) * 2 * N + ky) * (N / 2 + 1) + (CB * cb + lc);
+        cr[o] = c;
+        cr[o + static_cast<size_t>(N) * (N / 2 + 1)] = make_float2(0.5f * (a.y + bb.y), -0.5f * (a.x - bb.x));
+      }
       if (dc_col) {
         const float2 a2 = slab[(R2 * k1 + k2) * LS + CB];
         const float2 b2 = slab[G::rho(nky) * LS + CB];
         const float2 c2 = make_float2(0.5f * fmaf(a2.x, b2.y, a2.y * b2.x),
                                       0.25f * ((a2.x * a2.x + a2.y * a2.y) - (b2.x * b2.x + b2.y * b2.y)));
+        if constexpr (SAVE) {
+          const size_t o = (static_cast<size_t>(s) * 2 * N + ky) * (N / 2 + 1) + N / 2;
+          cr[o] = c2;
+          cr[o + static_cast<size_t>(N) * (N / 2 + 1)] = make_float2(0.5f * (a2.y + b2.y), -0.5f * (a2.x - b2.x));
+        }
         const float mq = fmaf(c2.x, c2.x, c2.y * c2.y);
         const float sq = mq > 0.f ? exp2f(half_w * log2f(mq)) * inv_n2 : 0.f;
         if (ky == 0) g = make_float2(0.f, 0.f);  // G[0,0] = 0
@@ -631,6 +649,34 @@ __global__ void __launch_bounds__(256) stream_final_kernel(const MatchLaunch L, 
     r.reserved = 0;
     *out = r;
   }
+}
+
+// ---------------------------------------------------------------------------
+// dynamic shared-memory sizes of the streaming kernels
+// ---------------------------------------------------------------------------
+template <int N, typename TIn>
+constexpr size_t rows_smem() {
+  using G = StreamGeom<N>;
+  return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * N + 2 * sizeof(TIn) * G::RB * N;
+}
+template <int N>
+constexpr size_t cols_smem() {
+  using G = StreamGeom<N>;
+  return sizeof(float2) * (N * (2 * G::CB + 8) + 2 * N);
+}
+template <int N>
+constexpr size_t irows_smem() {
+  using G = StreamGeom<N>;
+  return sizeof(float2) * (G::PB * G::RS + N);
+}
+
+// dynamic shared-memory opt-in, once per device and kernel
+template <typename K>
+inline cudaError_t smem_optin(K kern, size_t bytes, unsigned& done_mask, int dev) {
+  if (dev < 32 && (done_mask & (1u << dev))) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess && dev < 32) done_mask |= 1u << dev;
+  return e;
 }
 
 }  // namespace swift
