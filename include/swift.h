@@ -218,6 +218,34 @@ swift_status swift_match_batch_noalloc(const swift_level* level, swift_dtype in,
 swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, const float* grad_peak,
                                   const float* grad_snr, float* grad_affine, float* grad_w, void* stream);
 
+/* Forward schedules of a level.
+ *   FUSED   one persistent kernel: each window's field lives in the shared
+ *           memory of one CTA (64 x 64) or of a cluster of 2 (128 x 128) or
+ *           8 (256 x 256) CTAs, with the row/column redistributions through
+ *           distributed shared memory
+ *   STREAM  five kernels of independent CTAs passing each window's
+ *           intermediates through the plan's workspace
+ *   DEFAULT FUSED for 64 x 64, STREAM for larger windows */
+typedef enum { SWIFT_SCHED_DEFAULT = 0, SWIFT_SCHED_FUSED = 1, SWIFT_SCHED_STREAM = 2 } swift_schedule;
+
+/* Choose the forward schedule of one level. */
+swift_status swift_plan_set_schedule(swift_plan plan, int32_t level, int32_t schedule);
+
+/* Autotuner: times every schedule of every level present in `batch` on this
+ * batch (CUDA events; synchronises the host) and keeps the fastest for later
+ * calls.  `chosen` (host int32 [n_levels], may be NULL) receives the picks.
+ * On return `out` holds the batch's results under the chosen schedules. */
+swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swift_result* out, void* stream,
+                                 int32_t* chosen);
+
+/* Capture one forward call on `batch` (all its levels) into a CUDA graph
+ * owned by the plan; swift_plan_replay then re-runs it with one graph
+ * launch.  Pointers and sizes are baked into the graph: replay matches the
+ * same buffers (whose contents may change).  `stream` must not be the legacy
+ * default stream.  A new capture replaces the previous one. */
+swift_status swift_plan_capture(swift_plan plan, const swift_batch* batch, swift_result* out, void* stream);
+swift_status swift_plan_replay(swift_plan plan, void* stream);
+
 /* Set the whitening exponent of one level for later calls (w in [0, 1]). */
 swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w);
 

@@ -140,6 +140,37 @@ class Plan:
                         None if affine is None else affine.data_ptr())
         return bt, (ri, mi), B, refs[0].device
 
+    def set_schedule(self, level: int, schedule: str):
+        """Forward schedule of one level: "fused", "stream" or "default"."""
+        check(lib.swift_plan_set_schedule(self._h, int(level), _lib.SCHEDULE[schedule]), "swift_plan_set_schedule")
+
+    def autotune(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None):
+        """Time every schedule of every level on this batch, keep the fastest;
+        returns the chosen schedule names per level."""
+        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, None)
+        if out is None:
+            out = torch.empty((B, 8), dtype=torch.int32, device=dev)
+        chosen = (C.c_int32 * len(self.levels))()
+        check(lib.swift_plan_autotune(self._h, C.byref(bt), out.data_ptr(), _stream_ptr(stream), chosen),
+              "swift_plan_autotune")
+        names = {v: k for k, v in _lib.SCHEDULE.items()}
+        return [names[int(c)] for c in chosen], out
+
+    def capture(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None):
+        """Capture one forward call into a CUDA graph (see replay)."""
+        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, None)
+        if out is None:
+            out = torch.empty((B, 8), dtype=torch.int32, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        check(lib.swift_plan_capture(self._h, C.byref(bt), out.data_ptr(), _stream_ptr(stream)),
+              "swift_plan_capture")
+        return out
+
+    def replay(self, stream=None):
+        """Re-run the captured forward call with one graph launch."""
+        check(lib.swift_plan_replay(self._h, _stream_ptr(stream)), "swift_plan_replay")
+
     def backward(self, ref, mov, ref_origin, mov_origin, grad_peak, grad_snr, affine=None, level=None,
                  stream=None):
         """Gradients of sum(grad_peak * peak + grad_snr * snr) with respect to

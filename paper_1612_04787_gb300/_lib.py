@@ -23,6 +23,7 @@ SWIFT_ERR_CAPACITY = 6
 APOD = {"none": 0, "hann": 1, "tukey": 2}
 DTYPE = {"u8": 0, "f32": 1}
 PRECISION = {"fp32": 0, "bf16x2": 1, "fp16x2": 2}
+SCHEDULE = {"default": 0, "fused": 1, "stream": 2}
 
 WIN_OK, WIN_OUT_OF_BOUNDS, WIN_FLAT, WIN_NONFINITE = 0, 1, 2, 3
 
@@ -34,6 +35,10 @@ EXPORTS = (
     "swift_match_batch_noalloc",
     "swift_match_backward",
     "swift_plan_set_whitening",
+    "swift_plan_set_schedule",
+    "swift_plan_autotune",
+    "swift_plan_capture",
+    "swift_plan_replay",
     "swift_status_string",
     "swift_version",
 )
@@ -84,6 +89,15 @@ def _load():
     lib.swift_match_backward.restype = C.c_int
     lib.swift_plan_set_whitening.argtypes = [C.c_void_p, C.c_int32, C.c_float]
     lib.swift_plan_set_whitening.restype = C.c_int
+    lib.swift_plan_set_schedule.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+    lib.swift_plan_set_schedule.restype = C.c_int
+    lib.swift_plan_autotune.argtypes = [C.c_void_p, C.POINTER(SwiftBatch), C.c_void_p, C.c_void_p,
+                                        C.POINTER(C.c_int32)]
+    lib.swift_plan_autotune.restype = C.c_int
+    lib.swift_plan_capture.argtypes = [C.c_void_p, C.POINTER(SwiftBatch), C.c_void_p, C.c_void_p]
+    lib.swift_plan_capture.restype = C.c_int
+    lib.swift_plan_replay.argtypes = [C.c_void_p, C.c_void_p]
+    lib.swift_plan_replay.restype = C.c_int
     lib.swift_status_string.argtypes = [C.c_int]
     lib.swift_status_string.restype = C.c_char_p
     lib.swift_version.argtypes = []

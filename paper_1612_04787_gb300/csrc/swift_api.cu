@@ -60,6 +60,9 @@ struct swift_plan_s {
   void* bwork = nullptr;
   long long bwork_windows = 0;
   double* gw_acc = nullptr;  // [kMaxLevels] accumulated dL/dw
+  // one captured forward call (swift_plan_capture / swift_plan_replay)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace {
@@ -83,6 +86,8 @@ static swift_status release(swift_plan p) {
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
   if (p->work) cudaFree(p->work);
   if (p->bwork) cudaFree(p->bwork);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
   if (p->gw_acc) cudaFree(p->gw_acc);
   if (cur != p->device) cudaSetDevice(cur);
   delete p;
@@ -155,13 +160,12 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
     }
   }
   // workspace of the streaming forward path
+  // sized for the largest level, so any level can be switched to streaming
   size_t per = 0;
   for (int l = 0; l < n_levels; ++l) {
     p->stream_level[l] = default_stream(levels[l].n) ? 1 : 0;
-    if (p->stream_level[l]) {
-      const size_t b = swift::stream_bytes_per_window(levels[l].n);
-      per = b > per ? b : per;
-    }
+    const size_t b = swift::stream_bytes_per_window(levels[l].n);
+    per = b > per ? b : per;
   }
   if (per > 0) {
     p->work_windows = max_windows < kStreamSlice ? max_windows : kStreamSlice;
@@ -186,6 +190,54 @@ static bool image_ok(const swift_image& im, int n, int patch_mode, int64_t B) {
   if (im.height < 1 || im.width < 1 || im.pitch < im.width) return false;
   if (im.count > 1 && im.stride < im.pitch * im.height) return false;
   return true;
+}
+
+// Launch the windows of level l with the level's schedule (fused or streaming).
+static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, swift_result* out, cudaStream_t st) {
+  const int64_t B = batch->n_windows;
+  const int pm = batch->patch_mode ? 1 : 0;
+  const swift_level& lv = plan->levels[l];
+  const swift_image& ri = batch->ref[l];
+  const swift_image& mi = batch->mov[l];
+  swift::MatchLaunch L;
+  L.ref = ri.data;
+  L.mov = mi.data;
+  L.ref_pitch = pm ? lv.n : ri.pitch;
+  L.mov_pitch = pm ? lv.n : mi.pitch;
+  L.ref_stride = pm ? (ri.stride ? ri.stride : static_cast<long long>(lv.n) * lv.n) : ri.stride;
+  L.mov_stride = pm ? (mi.stride ? mi.stride : static_cast<long long>(lv.n) * lv.n) : mi.stride;
+  L.ref_h = ri.height;
+  L.ref_w = ri.width;
+  L.mov_h = mi.height;
+  L.mov_w = mi.width;
+  L.ref_count = ri.count;
+  L.patch_mode = pm;
+  L.ref_origin = batch->ref_origin;
+  L.mov_origin = batch->mov_origin;
+  L.level_idx = batch->level;
+  L.level = l;
+  L.n_windows = B;
+  L.w = lv.whiten_exponent;
+  const double r2 = static_cast<double>(lv.snr_exclusion_radius) * lv.snr_exclusion_radius;
+  L.radius2 = static_cast<float>(floor(r2));
+  L.inv_sum_a = plan->inv_sum_a[l];
+  L.taper = plan->taper[l];
+  L.twiddle = plan->twiddle[size_slot(lv.n)];
+  L.out = out;
+  if (plan->stream_level[l]) {
+    for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
+      const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
+      const swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
+      if (swift::launch_stream(lv.n, plan->dtype, L, W, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+    }
+    return SWIFT_OK;
+  }
+  const bool bulk = plan->dtype == SWIFT_IN_U8 && !pm && ri.count == 1 &&
+                    (reinterpret_cast<uintptr_t>(ri.data) % 16) == 0 &&
+                    (reinterpret_cast<uintptr_t>(mi.data) % 16) == 0 && ri.pitch % 16 == 0 &&
+                    mi.pitch % 16 == 0 && ri.width % 16 == 0 && mi.width % 16 == 0;
+  if (swift::launch_forward(lv.n, plan->dtype, bulk, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+  return SWIFT_OK;
 }
 
 static swift_status check_warp_batch(swift_plan plan, const swift_batch* batch);
@@ -216,47 +268,8 @@ extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* ba
     return warp_forward(plan, batch, out, st);
   }
   for (int l = 0; l < used_levels; ++l) {
-    const swift_level& lv = plan->levels[l];
-    const swift_image& ri = batch->ref[l];
-    const swift_image& mi = batch->mov[l];
-    swift::MatchLaunch L;
-    L.ref = ri.data;
-    L.mov = mi.data;
-    L.ref_pitch = pm ? lv.n : ri.pitch;
-    L.mov_pitch = pm ? lv.n : mi.pitch;
-    L.ref_stride = pm ? (ri.stride ? ri.stride : static_cast<long long>(lv.n) * lv.n) : ri.stride;
-    L.mov_stride = pm ? (mi.stride ? mi.stride : static_cast<long long>(lv.n) * lv.n) : mi.stride;
-    L.ref_h = ri.height;
-    L.ref_w = ri.width;
-    L.mov_h = mi.height;
-    L.mov_w = mi.width;
-    L.ref_count = ri.count;
-    L.patch_mode = pm;
-    L.ref_origin = batch->ref_origin;
-    L.mov_origin = batch->mov_origin;
-    L.level_idx = batch->level;
-    L.level = l;
-    L.n_windows = B;
-    L.w = lv.whiten_exponent;
-    const double r2 = static_cast<double>(lv.snr_exclusion_radius) * lv.snr_exclusion_radius;
-    L.radius2 = static_cast<float>(floor(r2));
-    L.inv_sum_a = plan->inv_sum_a[l];
-    L.taper = plan->taper[l];
-    L.twiddle = plan->twiddle[size_slot(lv.n)];
-    L.out = out;
-    if (plan->stream_level[l]) {
-      for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
-        const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
-        const swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
-        if (swift::launch_stream(lv.n, plan->dtype, L, W, st) != cudaSuccess) return SWIFT_ERR_CUDA;
-      }
-      continue;
-    }
-    const bool bulk = plan->dtype == SWIFT_IN_U8 && !pm && ri.count == 1 &&
-                      (reinterpret_cast<uintptr_t>(ri.data) % 16) == 0 &&
-                      (reinterpret_cast<uintptr_t>(mi.data) % 16) == 0 && ri.pitch % 16 == 0 &&
-                      mi.pitch % 16 == 0 && ri.width % 16 == 0 && mi.width % 16 == 0;
-    if (swift::launch_forward(lv.n, plan->dtype, bulk, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+    const swift_status e = run_level(plan, batch, l, out, st);
+    if (e != SWIFT_OK) return e;
   }
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   return SWIFT_OK;
@@ -383,6 +396,104 @@ extern "C" swift_status swift_match_backward(swift_plan plan, const swift_batch*
   }
   if (swift::launch_wout(plan->gw_acc, grad_w, plan->n_levels, st) != cudaSuccess) return SWIFT_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_schedule(swift_plan plan, int32_t level, int32_t schedule) {
+  if (!plan || level < 0 || level >= plan->n_levels) return SWIFT_ERR_INVALID_ARG;
+  if (schedule == SWIFT_SCHED_DEFAULT) {
+    plan->stream_level[level] = default_stream(plan->levels[level].n) ? 1 : 0;
+  } else if (schedule == SWIFT_SCHED_FUSED || schedule == SWIFT_SCHED_STREAM) {
+    plan->stream_level[level] = schedule == SWIFT_SCHED_STREAM ? 1 : 0;
+  } else {
+    return SWIFT_ERR_INVALID_ARG;
+  }
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swift_result* out,
+                                            void* stream, int32_t* chosen) {
+  if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
+  if (batch->affine) return SWIFT_ERR_INVALID_ARG;
+  // run once with the current schedules: validates the batch and warms up
+  swift_status e = swift_match_batch(plan, batch, out, stream);
+  if (e != SWIFT_OK) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return SWIFT_ERR_CUDA;
+  }
+  const int used = batch->level ? plan->n_levels : 1;
+  e = SWIFT_OK;
+  for (int l = 0; l < used && e == SWIFT_OK; ++l) {
+    float best = 3.4e38f;
+    int best_sched = plan->stream_level[l];
+    for (int sched = 0; sched < 2 && e == SWIFT_OK; ++sched) {
+      plan->stream_level[l] = sched;
+      if ((e = run_level(plan, batch, l, out, st)) != SWIFT_OK) break;  // warm-up
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3 && e == SWIFT_OK; ++rep) e = run_level(plan, batch, l, out, st);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        e = SWIFT_ERR_CUDA;
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_sched = sched;
+      }
+    }
+    plan->stream_level[l] = best_sched;
+    if (chosen) chosen[l] = best_sched ? SWIFT_SCHED_STREAM : SWIFT_SCHED_FUSED;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != SWIFT_OK) return e;
+  // leave `out` holding the results of the chosen schedules
+  return swift_match_batch(plan, batch, out, stream);
+}
+
+extern "C" swift_status swift_plan_capture(swift_plan plan, const swift_batch* batch, swift_result* out,
+                                           void* stream) {
+  if (!plan || !batch || !stream) return SWIFT_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // an uncaptured call first: checks the batch and does every one-time set-up
+  swift_status e = swift_match_batch(plan, batch, out, stream);
+  if (e != SWIFT_OK) return e;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SWIFT_ERR_CUDA;
+  if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  plan->graph_exec = nullptr;
+  plan->graph = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SWIFT_ERR_CUDA;
+  e = swift_match_batch(plan, batch, out, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &g);
+  if (e != SWIFT_OK || ce != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return e != SWIFT_OK ? e : SWIFT_ERR_CUDA;
+  }
+  cudaGraphExec_t x = nullptr;
+  if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return SWIFT_ERR_CUDA;
+  }
+  plan->graph = g;
+  plan->graph_exec = x;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_replay(swift_plan plan, void* stream) {
+  if (!plan || !plan->graph_exec) return SWIFT_ERR_INVALID_ARG;
+  if (cudaGraphLaunch(plan->graph_exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return SWIFT_ERR_CUDA;
+  }
   return SWIFT_OK;
 }
 

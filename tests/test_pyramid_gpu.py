@@ -1,0 +1,104 @@
+"""Mixed-size pyramid batches: schedules, the autotuner, and CUDA-graph replay.
+
+Pyramid stand-in: one EM-like section pair and its 2x and 4x box
+downsamples (powers-of-two pyramid, Sec. III "iscale"), windows of 64, 128
+and 256 px at stride n/4, whitening exponents 0.5 / 0.65 / 0.8 per level.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import swim
+from parity import compare, oracle_window
+
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1612_04787_gb300 as swift  # noqa: E402
+
+DEV = "cuda:0"
+LEVELS = [swift.Level(64, 0.5), swift.Level(128, 0.65), swift.Level(256, 0.8)]
+
+
+@pytest.fixture(scope="module")
+def pyramid():
+    a, b = synth.em_section_pair(1024, seed_content=51, seed_warp=52, seed_noise=(53, 54))
+    imgs_a = [synth.box_downsample(a, 4), synth.box_downsample(a, 2), a]
+    imgs_b = [synth.box_downsample(b, 4), synth.box_downsample(b, 2), b]
+    orgs, lvls = [], []
+    for k, (img, lv) in enumerate(zip(imgs_a, LEVELS)):
+        o = synth.grid_origins(img.shape[0], lv.n, lv.n // 4)
+        orgs.append(o)
+        lvls.append(np.full(len(o), k, np.int32))
+    org = np.concatenate(orgs).astype(np.int32)
+    lvl = np.concatenate(lvls)
+    perm = np.random.default_rng(55).permutation(len(org))
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)  # noqa: E731
+    return dict(a=imgs_a, b=imgs_b, org=org[perm], lvl=lvl[perm],
+                ta=[T(x) for x in imgs_a], tb=[T(x) for x in imgs_b], to=T(org[perm]), tl=T(lvl[perm]))
+
+
+def _oracle_check(P, g, idx):
+    for i in idx:
+        l = int(P["lvl"][i])
+        lv = LEVELS[l]
+        olv = swim.Level(lv.n, lv.whiten_exponent, swim.APOD_HANN, 1.0, lv.snr_exclusion_radius)
+        o, tied = oracle_window(swim.gather(P["b"][l], P["org"][i], lv.n), swim.gather(P["a"][l], P["org"][i], lv.n), olv)
+        compare(g, i, o, tied, lv.n, f"pyramid level {l}")
+
+
+def _close(g1, g2):
+    ok = (g1["status"] == 0) & (g2["status"] == 0)
+    assert (g1["status"] == g2["status"]).all()
+    same_peak = (g1["dy"] == g2["dy"]) & (g1["dx"] == g2["dx"])
+    assert same_peak[ok].mean() > 0.995  # near-ties may flip between schedules
+    sel = ok & same_peak
+    assert np.abs(g1["sx"][sel] - g2["sx"][sel]).max() <= 0.02
+    assert (np.abs(g1["snr"][sel] - g2["snr"][sel]) <= 1e-3 * np.abs(g2["snr"][sel])).all()
+
+
+@pytest.mark.parametrize("sched", [("fused", "fused", "fused"), ("stream", "stream", "stream"), ("stream", "fused", "stream")])
+def test_every_schedule_matches_the_oracle(pyramid, sched):
+    P = pyramid
+    plan = swift.Plan(LEVELS, dtype="u8", max_windows=len(P["org"]))
+    for l, s in enumerate(sched):
+        plan.set_schedule(l, s)
+    g = swift.decode(plan.match(P["ta"], P["tb"], P["to"], P["to"], level=P["tl"]))
+    assert (g["status"] == 0).all()
+    rng = np.random.default_rng(len(sched[0]))
+    idx = np.concatenate([rng.choice(np.nonzero(P["lvl"] == l)[0], 6, replace=False) for l in range(3)])
+    _oracle_check(P, g, idx)
+
+
+def test_autotune_then_graph_replay(pyramid):
+    P = pyramid
+    plan = swift.Plan(LEVELS, dtype="u8", max_windows=len(P["org"]))
+    base = swift.decode(plan.match(P["ta"], P["tb"], P["to"], P["to"], level=P["tl"]))
+    chosen, out = plan.autotune(P["ta"], P["tb"], P["to"], P["to"], level=P["tl"])
+    assert len(chosen) == 3 and all(c in ("fused", "stream") for c in chosen)
+    tuned = swift.decode(out)
+    _close(tuned, base)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        out_g = plan.capture(P["ta"], P["tb"], P["to"], P["to"], level=P["tl"], stream=stream)
+        ref = swift.decode(out_g).copy() if False else None
+        out_g.fill_(-1)
+        plan.replay(stream)
+    stream.synchronize()
+    g1 = swift.decode(out_g)
+    direct = swift.decode(plan.match(P["ta"], P["tb"], P["to"], P["to"], level=P["tl"]))
+    for k in g1:
+        assert (g1[k] == direct[k]).all(), k
+    # new contents in the same buffers: replay follows them
+    with torch.cuda.stream(stream):
+        for t in P["tb"]:
+            t.copy_(torch.roll(t, shifts=(3, -2), dims=(0, 1)))
+        plan.replay(stream)
+    stream.synchronize()
+    g2 = swift.decode(out_g)
+    direct2 = swift.decode(plan.match(P["ta"], P["tb"], P["to"], P["to"], level=P["tl"]))
+    for k in g2:
+        assert (g2[k] == direct2[k]).all(), k
+    assert not (g2["dx"] == g1["dx"]).all()
