@@ -1,15 +1,26 @@
 """Throughput of the block-matching step on one GB300 (or N, one rank per GPU).
 
-Workload (default): a 31 x 31 grid of 256 x 256 windows at stride 128 on a pair
-of 4096 x 4096 uint8 EM-like sections (the second warped by a small random
-affine plus a smooth displacement field), whitening exponent 0.65, Hann taper,
-SNR exclusion radius 3 px: 961 window pairs per step.  Synthetic stand-ins for
-the paper's ssEM sections (generated by ``synth``).
+Default workload (the headline metric): a 31 x 31 grid of 256 x 256 windows at
+stride 128 on a pair of 4096 x 4096 uint8 EM-like sections (the second warped
+by a small random affine plus a smooth displacement field), whitening exponent
+0.65, Hann taper, SNR exclusion radius 3 px: 961 window pairs per step.
+Other workloads (``--workload``):
 
-Timing: W warm-up steps, then K timed steps; L2 is flushed (256 MiB write)
-before every timed step, outside the CUDA events that time the step itself.
-Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
-host cores instead (the reference arm; there is no upstream code).
+  noise64     the 64 x 64 worked example (blurred noise shifted by (-3, +5)), one pair
+  pyramid     the same section pair at 1024^2 / 2048^2 / 4096^2 with 64 / 128 / 256
+              windows at stride n/4 (11,163 windows), w = 0.5 / 0.65 / 0.8, schedules
+              picked by the autotuner, every step one CUDA-graph replay
+  patches128  8192 float32 128 x 128 patch pairs with known subpixel shifts (1 GiB)
+  patches256  8192 float32 256 x 256 patch pairs (4 GiB)
+  warp        2048 windows of 128 x 128 on a 9-section stack: reference = mean of the
+              8 neighbours, moving = resampled under per-window affine warps; a step is
+              the forward and the backward of loss = -sum snr * peak
+
+All inputs are seeded synthetic stand-ins for the paper's ssEM sections
+(``synth``).  Timing: W warm-up steps, then K timed steps; L2 is flushed (256 MiB
+write) before every timed step, outside the CUDA events that time the step.
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the host
+cores instead (the reference arm: there is no upstream code to run).
 """
 from __future__ import annotations
 
@@ -30,11 +41,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "match windows/sec (256² whitened FFT correlations) & % roofline vs plain FP32"
-N_WIN = 256
-STRIDE = 128
-SECTION = 4096
-W_EXP = 0.65
-RADIUS = 3.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -42,31 +48,26 @@ SM_MAX_MHZ = 2070.0
 
 def flops_per_pair(n: int) -> float:
     """Algorithmic FP32 work of one window pair: three real 2D FFTs counted as
-    2.5 * M * log2(M) each (M = n^2 points; 5 M log2 M per complex transform,
-    half for real data) plus ~30 flops per pixel for taper, mean, whitening
-    (two transcendental ops per bin) and the reductions."""
+    2.5 * M * log2(M) each (M = n^2; 5 M log2 M per complex transform, half for
+    real data) plus ~30 flops per pixel for taper, mean, whitening (two
+    transcendental ops per bin) and the reductions."""
     m = n * n
     return 7.5 * m * math.log2(m) + 30.0 * m
 
 
+def kernel_flops(n: int) -> dict:
+    """The same work split over the streaming kernels: rows = the row transforms
+    of z = m' + i r' (one complex 2D half), cols = the forward column transforms
+    plus the inverse columns for kx <= n/2 plus unpack and whitening, irows =
+    the paired inverse rows, stats and final = the statistics and reductions."""
+    m = n * n
+    half = 5.0 * m * math.log2(n)  # n complex FFTs of length n
+    return {"stats": 2.5 * m, "rows": half + 5.0 * m, "cols": 1.5 * half + 15.0 * m,
+            "irows": 0.5 * half + 5.0 * m, "final": 2.5 * m, "fused": flops_per_pair(n)}
+
+
 def fp32_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
     return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-
-
-def workload_description():
-    return (f"{(SECTION - N_WIN) // STRIDE + 1}x{(SECTION - N_WIN) // STRIDE + 1} grid of {N_WIN}x{N_WIN} "
-            f"windows (stride {STRIDE}) on a {SECTION}x{SECTION} uint8 EM-like section pair")
-
-
-def make_inputs(pairs: int = 1):
-    import synth
-    secs = []
-    for p in range(pairs):
-        a, b = synth.em_section_pair(SECTION, seed_content=0 + 10 * p, seed_warp=1 + 10 * p,
-                                     seed_noise=(2 + 10 * p, 3 + 10 * p))
-        secs.append((a, b))
-    org = synth.grid_origins(SECTION, N_WIN, STRIDE)
-    return secs, org
 
 
 # --------------------------------------------------------------------------- #
@@ -133,7 +134,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_key: str):
+def recorded_traffic(kernel_key: str, windows_per_launch: int):
+    """DRAM bytes per launch from a committed ncu capture, scaled to this
+    launch's windows (traffic grows in proportion), or None when the kernel
+    sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -143,35 +147,31 @@ def recorded_traffic(kernel_key: str):
         return None
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec["dram_bytes_per_window"] * windows_per_launch
 
 
 # --------------------------------------------------------------------------- #
 # oracle timing on the host cores (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------- #
 def _oracle_chunk(args):
-    mov, ref = args
+    mov, ref, n, w, r = args
     from oracle import swim
-    lv = swim.Level(N_WIN, W_EXP, swim.APOD_HANN, 1.0, RADIUS)
-    return [swim.match_pair(m, r, lv)["status"] for m, r in zip(mov, ref)]
+    lv = swim.Level(n, w, swim.APOD_HANN, 1.0, r)
+    return [swim.match_pair(m, rr, lv)["status"] for m, rr in zip(mov, ref)]
 
 
-def oracle_throughput(secs, org, sample: int):
-    """Windows/s of the FP64 oracle over the first ``sample`` windows, one
-    single-threaded worker process per host core (spawned)."""
-    a, b = secs[0]
-    idx = np.arange(min(sample, len(org)))
-    movs = [b[o[0]:o[0] + N_WIN, o[1]:o[1] + N_WIN].astype(np.float64) for o in org[idx]]
-    refs = [a[o[0]:o[0] + N_WIN, o[1]:o[1] + N_WIN].astype(np.float64) for o in org[idx]]
+def oracle_throughput(movs, refs, n, w, r):
+    """Windows/s of the FP64 oracle over the given windows, one single-threaded
+    worker process per host core (spawned)."""
     cores = len(os.sched_getaffinity(0))
-    chunks = [(movs[i::cores], refs[i::cores]) for i in range(cores)]
+    chunks = [(movs[i::cores], refs[i::cores], n, w, r) for i in range(cores)]
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"
     try:
         ctx = mp.get_context("spawn")
         with ctx.Pool(cores) as pool:
-            pool.map(_oracle_chunk, [([m], [r]) for m, r in zip(movs[:cores], refs[:cores])])  # warm
+            pool.map(_oracle_chunk, [([m], [rr], n, w, r) for m, rr in zip(movs[:cores], refs[:cores])])
             t0 = time.perf_counter()
             pool.map(_oracle_chunk, chunks)
             dt = time.perf_counter() - t0
@@ -181,7 +181,319 @@ def oracle_throughput(secs, org, sample: int):
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    return len(idx) / dt, cores, dt
+    return len(movs) / dt, cores, dt
+
+
+# --------------------------------------------------------------------------- #
+# workloads
+# --------------------------------------------------------------------------- #
+class Sections:
+    name = "sections"
+    dominant_n = 256
+
+    def __init__(self, torch, swift, dev, pairs=1, windows=0, precision="fp32"):
+        import synth
+        self.n, self.w, self.r, self.size, self.stride = 256, 0.65, 3.0, 4096, 128
+        self.secs = [synth.em_section_pair(self.size, seed_content=10 * p, seed_warp=1 + 10 * p,
+                                           seed_noise=(2 + 10 * p, 3 + 10 * p)) for p in range(pairs)]
+        org = synth.grid_origins(self.size, self.n, self.stride)
+        self.org = org[:windows] if windows > 0 else org
+        g = (self.size - self.n) // self.stride + 1
+        self.description = (f"{g}x{g} grid of {self.n}x{self.n} windows (stride {self.stride}) on a "
+                            f"{self.size}x{self.size} uint8 EM-like section pair")
+        self.B1 = len(self.org)
+        self.windows = self.B1 * pairs
+        self.plan = swift.Plan([swift.Level(self.n, self.w, "hann", 1.0, self.r)], dtype="u8",
+                               precision=precision, max_windows=self.B1)
+        self.d = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in self.secs]
+        self.dorg = torch.from_numpy(self.org).to(dev)
+        self.outs = [torch.empty((self.B1, 8), dtype=torch.int32, device=dev) for _ in self.secs]
+        self.h = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in self.secs]
+        self.horg = torch.from_numpy(self.org).pin_memory()
+        self.hout = [torch.empty((self.B1, 8), dtype=torch.int32).pin_memory() for _ in self.secs]
+        self.flops = flops_per_pair(self.n) * self.windows
+        self.launches_per_step = 5 * len(self.secs)
+        self.config = {"window": self.n, "windows_per_step": self.windows, "section_pairs_per_step": pairs,
+                       "whiten_exponent": self.w, "apod": "hann", "snr_exclusion_radius": self.r, "input": "uint8"}
+
+    def step(self, stream):
+        for (a, b), o in zip(self.d, self.outs):
+            self.plan.match(a, b, self.dorg, self.dorg, out=o, stream=stream)
+
+    def e2e_step(self, torch, stream):
+        self.dorg.copy_(self.horg, non_blocking=True)
+        for (ha, hb), (da, db), o, ho in zip(self.h, self.d, self.outs, self.hout):
+            da.copy_(ha, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            self.plan.match(da, db, self.dorg, self.dorg, out=o, stream=stream)
+            ho.copy_(o, non_blocking=True)
+        stream.synchronize()
+
+    def io_bytes(self):
+        return sum(a.nbytes + b.nbytes for a, b in self.secs) + self.org.nbytes, self.windows * 32
+
+    def ok_fraction(self, swift):
+        return float((swift.decode(self.outs[0])["status"] == 0).mean())
+
+    def oracle_windows(self, k):
+        a, b = self.secs[0]
+        o = self.org[:k]
+        n = self.n
+        return ([b[y:y + n, x:x + n].astype(np.float64) for y, x in o],
+                [a[y:y + n, x:x + n].astype(np.float64) for y, x in o], n, self.w, self.r)
+
+
+class Noise64:
+    name = "noise64"
+    dominant_n = 64
+
+    def __init__(self, torch, swift, dev, **_):
+        import synth
+        self.n, self.w, self.r = 64, 0.65, 3.0
+        ref, mov = synth.noise_pair(64, (-3, 5))
+        self.ref, self.mov = ref.astype(np.float32)[None], mov.astype(np.float32)[None]
+        self.description = "64x64 worked example: blurred seed-0 noise and its (-3, +5) shift plus noise, one pair"
+        self.windows = 1
+        self.plan = swift.Plan([swift.Level(64, self.w, "hann", 1.0, self.r)], dtype="f32", max_windows=1)
+        self.dr, self.dm = torch.from_numpy(self.ref).to(dev), torch.from_numpy(self.mov).to(dev)
+        self.out = torch.empty((1, 8), dtype=torch.int32, device=dev)
+        self.hr, self.hm = torch.from_numpy(self.ref).pin_memory(), torch.from_numpy(self.mov).pin_memory()
+        self.hout = torch.empty((1, 8), dtype=torch.int32).pin_memory()
+        self.flops = flops_per_pair(64)
+        self.launches_per_step = 1
+        self.config = {"window": 64, "windows_per_step": 1, "whiten_exponent": self.w, "input": "float32"}
+
+    def step(self, stream):
+        self.plan.match(self.dr, self.dm, out=self.out, stream=stream)
+
+    def e2e_step(self, torch, stream):
+        self.dr.copy_(self.hr, non_blocking=True)
+        self.dm.copy_(self.hm, non_blocking=True)
+        self.plan.match(self.dr, self.dm, out=self.out, stream=stream)
+        self.hout.copy_(self.out, non_blocking=True)
+        stream.synchronize()
+
+    def io_bytes(self):
+        return self.ref.nbytes + self.mov.nbytes, 32
+
+    def ok_fraction(self, swift):
+        return float((swift.decode(self.out)["status"] == 0).mean())
+
+    def oracle_windows(self, k):
+        return [self.mov[0].astype(np.float64)], [self.ref[0].astype(np.float64)], 64, self.w, self.r
+
+
+class Pyramid:
+    name = "pyramid"
+    dominant_n = 256
+
+    def __init__(self, torch, swift, dev, **_):
+        import synth
+        a, b = synth.em_section_pair(4096)
+        self.imgs = [(synth.box_downsample(a, 4), synth.box_downsample(b, 4)),
+                     (synth.box_downsample(a, 2), synth.box_downsample(b, 2)), (a, b)]
+        self.levels = [swift.Level(64, 0.5), swift.Level(128, 0.65), swift.Level(256, 0.8)]
+        orgs, lvls = [], []
+        for k, ((ia, _), lv) in enumerate(zip(self.imgs, self.levels)):
+            o = synth.grid_origins(ia.shape[0], lv.n, lv.n // 4)
+            orgs.append(o)
+            lvls.append(np.full(len(o), k, np.int32))
+        self.org = np.concatenate(orgs).astype(np.int32)
+        self.lvl = np.concatenate(lvls)
+        self.windows = len(self.org)
+        self.description = (f"pyramid of one section pair at 1024^2 / 2048^2 / 4096^2 with 64 / 128 / 256 windows "
+                            f"at stride n/4 ({self.windows} windows), w = 0.5 / 0.65 / 0.8, one CUDA-graph "
+                            f"replay per step")
+        self.plan = swift.Plan(self.levels, dtype="u8", max_windows=self.windows)
+        T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)  # noqa: E731
+        self.da = [T(x[0]) for x in self.imgs]
+        self.db = [T(x[1]) for x in self.imgs]
+        self.dorg, self.dlvl = T(self.org), T(self.lvl)
+        self.chosen, _ = self.plan.autotune(self.da, self.db, self.dorg, self.dorg, level=self.dlvl)
+        self.cap_stream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(self.cap_stream):
+            self.out = self.plan.capture(self.da, self.db, self.dorg, self.dorg, level=self.dlvl,
+                                         stream=self.cap_stream)
+        self.cap_stream.synchronize()
+        self.flops = sum(flops_per_pair(lv.n) * int((self.lvl == k).sum()) for k, lv in enumerate(self.levels))
+        slices = -(-self.windows // 2048)  # the streaming schedule walks the batch in slices of 2048
+        self.launches_per_step = sum(1 if c == "fused" else 5 * slices for c in self.chosen)
+        self.h = [(torch.from_numpy(x[0]).pin_memory(), torch.from_numpy(x[1]).pin_memory()) for x in self.imgs]
+        self.hout = torch.empty((self.windows, 8), dtype=torch.int32).pin_memory()
+        self.config = {"windows_per_step": self.windows, "levels": [64, 128, 256],
+                       "whiten_exponent": [0.5, 0.65, 0.8], "schedules": self.chosen, "input": "uint8",
+                       "graph": "one cudaGraphLaunch per step"}
+
+    def step(self, stream):
+        self.plan.replay(stream=stream)
+
+    def e2e_step(self, torch, stream):
+        for (ha, hb), da, db in zip(self.h, self.da, self.db):
+            da.copy_(ha, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+        self.plan.replay(stream=stream)
+        self.hout.copy_(self.out, non_blocking=True)
+        stream.synchronize()
+
+    def io_bytes(self):
+        return sum(a.nbytes + b.nbytes for a, b in self.imgs), self.windows * 32
+
+    def ok_fraction(self, swift):
+        return float((swift.decode(self.out)["status"] == 0).mean())
+
+    def oracle_windows(self, k):
+        movs, refs = [], []
+        a, b = self.imgs[2]
+        for i in np.nonzero(self.lvl == 2)[0][:k]:
+            y, x = self.org[i]
+            movs.append(b[y:y + 256, x:x + 256].astype(np.float64))
+            refs.append(a[y:y + 256, x:x + 256].astype(np.float64))
+        return movs, refs, 256, 0.8, 3.0
+
+
+class Patches:
+    def __init__(self, torch, swift, dev, n=128, count=8192, precision="fp32", **_):
+        import synth
+        self.name = f"patches{n}"
+        self.dominant_n = n
+        self.n, self.w, self.r = n, 0.65, 3.0
+        a, _ = synth.em_section_pair(4096, seed_content=60, seed_warp=61, seed_noise=(62, 63))
+        self.ref, self.mov = self._make(torch, dev, a, n, count, seed=10 if n == 128 else 11)
+        self.windows = count
+        self.description = (f"{count} float32 {n}x{n} patch pairs cut from an EM-like section; moving = the 2n x 2n "
+                            f"tile shifted by U(+-20 px)^2 through a Fourier phase ramp, centre-cropped")
+        self.plan = swift.Plan([swift.Level(n, self.w, "hann", 1.0, self.r)], dtype="f32", precision=precision,
+                               max_windows=count)
+        self.out = torch.empty((count, 8), dtype=torch.int32, device=dev)
+        self.flops = flops_per_pair(n) * count
+        self.launches_per_step = 5 * ((count + 2047) // 2048)
+        self.hout = torch.empty((count, 8), dtype=torch.int32).pin_memory()
+        self.config = {"window": n, "windows_per_step": count, "input": "float32", "precision": precision,
+                       "whiten_exponent": self.w}
+
+    @staticmethod
+    def _make(torch, dev, section, n, count, seed):
+        """Reference = centre of a 2n tile; moving = the tile shifted by a known
+        subpixel d (phase ramp), centre-cropped (input generation, on the GPU)."""
+        rng = np.random.default_rng(seed)
+        m = 2 * n
+        oy = rng.integers(0, section.shape[0] - m + 1, count)
+        ox = rng.integers(0, section.shape[1] - m + 1, count)
+        d = rng.uniform(-20.0, 20.0, (count, 2))
+        sec = torch.from_numpy(section.astype(np.float32)).to(dev)
+        k = torch.fft.fftfreq(m, device=dev, dtype=torch.float64)
+        ref = torch.empty((count, n, n), dtype=torch.float32, device=dev)
+        mov = torch.empty((count, n, n), dtype=torch.float32, device=dev)
+        c0 = n // 2
+        for s in range(0, count, 512):
+            e = min(count, s + 512)
+            tiles = torch.stack([sec[oy[i]:oy[i] + m, ox[i]:ox[i] + m] for i in range(s, e)]).double()
+            dd = torch.from_numpy(d[s:e]).to(dev)
+            ramp = torch.exp(-2j * math.pi * (k[None, :, None] * dd[:, 0, None, None]
+                                               + k[None, None, :] * dd[:, 1, None, None]))
+            shifted = torch.fft.ifft2(torch.fft.fft2(tiles) * ramp).real
+            ref[s:e] = tiles[:, c0:c0 + n, c0:c0 + n].float()
+            mov[s:e] = shifted[:, c0:c0 + n, c0:c0 + n].float()
+        return ref.contiguous(), mov.contiguous()
+
+    def step(self, stream):
+        self.plan.match(self.ref, self.mov, out=self.out, stream=stream)
+
+    def e2e_step(self, torch, stream):
+        if not hasattr(self, "href"):
+            self.href, self.hmov = self.ref.cpu().pin_memory(), self.mov.cpu().pin_memory()
+        self.ref.copy_(self.href, non_blocking=True)
+        self.mov.copy_(self.hmov, non_blocking=True)
+        self.plan.match(self.ref, self.mov, out=self.out, stream=stream)
+        self.hout.copy_(self.out, non_blocking=True)
+        stream.synchronize()
+
+    def io_bytes(self):
+        return 2 * self.ref.numel() * 4, self.windows * 32
+
+    def ok_fraction(self, swift):
+        return float((swift.decode(self.out)["status"] == 0).mean())
+
+    def oracle_windows(self, k):
+        r = self.ref[:k].double().cpu().numpy()
+        m = self.mov[:k].double().cpu().numpy()
+        return list(m), list(r), self.n, self.w, self.r
+
+
+class Warp:
+    name = "warp"
+    dominant_n = 128
+
+    def __init__(self, torch, swift, dev, count=2048, **_):
+        import synth
+        self.n, self.w, self.r = 128, 0.65, 3.0
+        size = 2048
+        stack = synth.section_stack(size, depth=9, seed=20)
+        self.model = np.ascontiguousarray(stack[[0, 1, 2, 3, 5, 6, 7, 8]])
+        self.movsec = np.ascontiguousarray(stack[4])
+        self.org = synth.random_origins(count, size, size, self.n, seed=21, margin=8)
+        self.theta = synth.affine_params(count, seed=22)
+        self.windows = count
+        self.description = (f"{count} windows of 128x128 on a 9-section {size}^2 stack: reference = mean of the 8 "
+                            f"neighbours of section 4, moving = section 4 resampled under per-window affine warps "
+                            f"(offset +-2 px, rotation +-0.5 deg); step = forward + backward of -sum snr*peak")
+        self.plan = swift.Plan([swift.Level(self.n, self.w, "hann", 1.0, self.r)], dtype="u8", max_windows=count)
+        T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)  # noqa: E731
+        self.dm, self.ds = T(self.model), T(self.movsec)
+        self.dorg, self.dth = T(self.org), T(self.theta)
+        self.out = torch.empty((count, 8), dtype=torch.int32, device=dev)
+        self.flops = 3.0 * flops_per_pair(self.n) * count  # forward + (recomputed forward + adjoint)
+        slices = -(-count // 1024)  # warp / backward slices of 1024 windows
+        self.launches_per_step = slices * (1 + 5) + slices * (1 + 10) + 1
+        self.config = {"window": 128, "windows_per_step": count, "model_sections": 8, "input": "uint8",
+                       "step": "forward + backward"}
+
+    def step(self, stream):
+        import torch
+        self.plan.match(self.dm, self.ds, self.dorg, self.dorg, out=self.out, stream=stream, affine=self.dth)
+        f = self.out.view(torch.float32)
+        self.plan.backward(self.dm, self.ds, self.dorg, self.dorg, -f[:, 4], -f[:, 5], affine=self.dth,
+                           stream=stream)
+
+    def e2e_step(self, torch, stream):
+        if not hasattr(self, "hth"):
+            self.hth = torch.from_numpy(self.theta).pin_memory()
+            self.hg = torch.empty((self.windows, 6), dtype=torch.float32).pin_memory()
+        self.dth.copy_(self.hth, non_blocking=True)
+        self.plan.match(self.dm, self.ds, self.dorg, self.dorg, out=self.out, stream=stream, affine=self.dth)
+        f = self.out.view(torch.float32)
+        g, _ = self.plan.backward(self.dm, self.ds, self.dorg, self.dorg, -f[:, 4], -f[:, 5], affine=self.dth,
+                                  stream=stream)
+        self.hg.copy_(g, non_blocking=True)
+        stream.synchronize()
+
+    def io_bytes(self):
+        return self.theta.nbytes, self.windows * 6 * 4
+
+    def ok_fraction(self, swift):
+        return float((swift.decode(self.out)["status"] == 0).mean())
+
+    def oracle_windows(self, k):
+        from oracle import swim
+        movs, refs = [], []
+        for i in range(k):
+            movs.append(swim.resample(self.movsec, self.org[i], self.n, self.theta[i].astype(np.float64)))
+            refs.append(swim.project(list(self.model), self.org[i], self.n))
+        return movs, refs, self.n, self.w, self.r
+
+
+def make_workload(name, torch, swift, dev, args):
+    if name == "sections":
+        return Sections(torch, swift, dev, pairs=args.pairs, windows=args.windows, precision=args.precision)
+    if name == "noise64":
+        return Noise64(torch, swift, dev)
+    if name == "pyramid":
+        return Pyramid(torch, swift, dev)
+    if name in ("patches128", "patches256"):
+        return Patches(torch, swift, dev, n=int(name[7:]), count=args.windows or 8192, precision=args.precision)
+    if name == "warp":
+        return Warp(torch, swift, dev, count=args.windows or 2048)
+    raise ValueError(name)
 
 
 # --------------------------------------------------------------------------- #
@@ -192,43 +504,59 @@ def dist_setup():
     return world, rank, local
 
 
+def reference_arm(args):
+    """The FP64 oracle timed on the host cores (no GPU)."""
+    import synth
+    n, w, r = 256, 0.65, 3.0
+    a, b = synth.em_section_pair(4096)
+    org = synth.grid_origins(4096, 256, 128)[: args.oracle_sample]
+    movs = [b[y:y + n, x:x + n].astype(np.float64) for y, x in org]
+    refs = [a[y:y + n, x:x + n].astype(np.float64) for y, x in org]
+    for _ in range(args.warmup):
+        oracle_throughput(movs[:64], refs[:64], n, w, r)
+    vals, cores = [], 0
+    for _ in range(args.steps):
+        v, cores, _dt = oracle_throughput(movs, refs, n, w, r)
+        vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(org) / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "31x31 grid of 256x256 windows (stride 128) on a 4096x4096 uint8 EM-like "
+                               "section pair", "windows_per_step": len(org)},
+        "cpu_baseline": {"value": value, "unit": "windows/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {len(org)} windows of the workload per step, FP64 direct-DFT oracle, "
+                                   f"one single-threaded process per core"},
+        "e2e": {"value": value, "unit": "windows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+KERNEL_NAMES = {"stats": "stream_stats_kernel", "rows": "stream_rows_kernel", "cols": "stream_cols_kernel",
+                "irows": "stream_irows_kernel", "final": "stream_final_kernel", "fused": "swim_forward_kernel"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (961 windows each)")
+    ap.add_argument("--workload", default="sections",
+                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2", "fp16x2"])
+    ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (sections workload)")
+    ap.add_argument("--windows", type=int, default=0, help="limit the windows per step (small profiling cases)")
     ap.add_argument("--oracle-sample", type=int, default=961)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--windows", type=int, default=0,
-                    help="use only the first K windows of the grid (small profiling cases)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        secs, org = make_inputs(1)
-        sample = min(args.oracle_sample, len(org))
-        vals = []
-        cores = 0
-        for _ in range(args.warmup):
-            oracle_throughput(secs, org, min(sample, 64))
-        for _ in range(args.steps):
-            v, cores, _dt = oracle_throughput(secs, org, sample)
-            vals.append(v)
-        value = statistics.median(vals)
-        line = {
-            "impl": "reference", "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / value,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_description(), "windows_per_step": sample},
-            "cpu_baseline": {"value": value, "unit": "windows/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {sample} windows of the workload per step"},
-            "e2e": {"value": value, "unit": "windows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }
-        print(json.dumps(line))
+        if rank == 0:
+            reference_arm(args)
         return
 
     import torch
@@ -240,27 +568,20 @@ def main():
     torch.cuda.set_device(dev)
     import paper_1612_04787_gb300 as swift
 
-    secs, org = make_inputs(args.pairs)
-    if args.windows > 0:
-        org = org[: args.windows]
-    B1 = len(org)
-    plan = swift.Plan([swift.Level(N_WIN, W_EXP, "hann", 1.0, RADIUS)], dtype="u8", max_windows=B1)
-    d_secs = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in secs]
-    d_org = torch.from_numpy(org).to(dev)
-    outs = [torch.empty((B1, 8), dtype=torch.int32, device=dev) for _ in secs]
+    W = make_workload(args.workload, torch, swift, dev, args)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        for (a, b), o in zip(d_secs, outs):
-            plan.match(a, b, d_org, d_org, out=o, stream=stream)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        W.step(stream)
     torch.cuda.synchronize(dev)
-    res = swift.decode(outs[0])
-    ok_frac = float((res["status"] == 0).mean())
+    ok_frac = W.ok_fraction(swift)
 
+    # per-kernel CUDA events around the library's launches (not under graph replay)
+    timing = args.workload not in ("pyramid", "warp")
+    if timing:
+        W.plan.set_timing(True)
+        W.plan.timings()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -272,75 +593,73 @@ def main():
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
-        step()
+        W.step(stream)
         ends[k].record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
+    kt = W.plan.timings() if timing else {}
+    if timing:
+        W.plan.set_timing(False)
     durs = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
     total_ms = sum(durs)
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    windows_per_step = B1 * len(secs)
-    value = world * windows_per_step * args.steps / (total_ms / 1e3)
-    print(f"[bench] rank {rank}: {args.steps} steps, {total_ms / args.steps:.4f} ms/step, "
+    value = world * W.windows * args.steps / (total_ms / 1e3)
+    print(f"[bench] {W.name} rank {rank}: {args.steps} steps, {total_ms / args.steps:.4f} ms/step, "
           f"{value:.1f} windows/s", file=sys.stderr, flush=True)
 
-    # e2e: pinned host sections -> device, match, results -> host, every step
-    h_secs = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in secs]
-    h_org = torch.from_numpy(org).pin_memory()
-    h_out = [torch.empty((B1, 8), dtype=torch.int32).pin_memory() for _ in secs]
-    e2e_steps = max(3, min(args.steps, 50))
-
-    def e2e_step():
-        d_o = d_org.copy_(h_org, non_blocking=True)
-        for (ha, hb), (da, db), o, ho in zip(h_secs, d_secs, outs, h_out):
-            da.copy_(ha, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            plan.match(da, db, d_o, d_o, out=o, stream=stream)
-            ho.copy_(o, non_blocking=True)
-        torch.cuda.synchronize(dev)
-
-    e2e_step()
+    # e2e through the public API with host buffers
+    e2e_steps = max(3, min(args.steps, 30))
+    W.e2e_step(torch, stream)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        e2e_step()
+        W.e2e_step(torch, stream)
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * windows_per_step * e2e_steps / e2e_s
-    h2d = sum(a.nbytes + b.nbytes for a, b in secs) + org.nbytes
-    d2h = windows_per_step * 32
+    e2e_value = world * W.windows * e2e_steps / e2e_s
+    h2d, d2h = W.io_bytes()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, dt = oracle_throughput(secs, org, args.oracle_sample)
+        movs, refs, n, w, r = W.oracle_windows(args.oracle_sample)
+        v, cores, dt = oracle_throughput(movs, refs, n, w, r)
         cpu = {"value": v, "unit": "windows/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {min(args.oracle_sample, B1)} of the {B1} windows, FP64 direct-DFT oracle, "
+               "sample": f"{len(movs)} windows of the workload ({n}x{n}), FP64 direct-DFT oracle, forward only, "
                          f"one single-threaded process per core ({dt:.1f} s)"}
 
-    kernel_ms = total_ms / (args.steps * len(secs))  # one launch per section pair per step
-    achieved = flops_per_pair(N_WIN) * B1 / (kernel_ms / 1e3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = recorded_traffic("swim_forward_kernel<256,4,u8>")
+    step_tflops = W.flops / (total_ms / args.steps / 1e3) / 1e12
+    if kt:
+        dom = max(kt, key=lambda k: kt[k][0])
+        launches = kt[dom][1]
+        dom_ms = kt[dom][0] / launches
+        windows_per_launch = W.windows * args.steps / launches
+        achieved = kernel_flops(W.dominant_n)[dom] * windows_per_launch / (dom_ms / 1e3) / 1e12
+        tot = sum(x[0] for x in kt.values())
+        shares = {k: round(v[0] / tot, 4) for k, v in kt.items()}
+        dom_name = KERNEL_NAMES[dom]
+    else:
+        dom_name, achieved, shares, windows_per_launch = "pipeline (graph replay)", step_tflops, None, W.windows
+    traffic = recorded_traffic(f"{dom_name}<{W.dominant_n}>", windows_per_launch)
     line = {
         "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_description(), "window": N_WIN, "windows_per_step": windows_per_step,
-                   "section_pairs_per_step": len(secs), "whiten_exponent": W_EXP, "apod": "hann",
-                   "snr_exclusion_radius": RADIUS, "input": "uint8",
-                   "l2": "flushed before every timed step (256 MiB write, outside the step's events)",
-                   "status_ok_fraction": ok_frac},
+        "config": dict({"workload": W.description, "name": W.name,
+                        "l2": "flushed before every timed step (256 MiB write, outside the step's events)",
+                        "status_ok_fraction": ok_frac}, **W.config),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "swim_forward_kernel<256,4,u8>",
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock), derived",
-                     "flops_per_window": flops_per_pair(N_WIN)},
+                     "kernel": f"{dom_name}<{W.dominant_n}>",
+                     "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
+                     "kernel_share_of_step": shares,
+                     "pipeline_tflops": step_tflops, "pipeline_frac": step_tflops / peak},
         "e2e": {"value": e2e_value, "unit": "windows/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": args.steps * len(secs),
+        "gpu_launches": args.steps * W.launches_per_step,
         "clocks": clocks,
     }
     if cpu is not None:

@@ -246,6 +246,17 @@ swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swif
 swift_status swift_plan_capture(swift_plan plan, const swift_batch* batch, swift_result* out, void* stream);
 swift_status swift_plan_replay(swift_plan plan, void* stream);
 
+/* Per-kernel timing.  While enabled, every forward launch records CUDA
+ * events on its stream around each kernel (a ring of 1024 launch records);
+ * swift_plan_timings synchronises on them and returns, per kernel slot, the
+ * summed device time in ms and the number of launches since the last read,
+ * then starts over.  Slots: 0 statistics, 1 row transforms, 2 column
+ * transforms + whitening, 3 inverse row transforms, 4 finalize (the
+ * streaming schedule), 5 fused kernel, 6-7 unused.  kernel_ms and launches
+ * are host arrays of 8. */
+swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
+swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, int32_t* launches);
+
 /* Set the whitening exponent of one level for later calls (w in [0, 1]). */
 swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w);
 

@@ -167,6 +167,19 @@ class Plan:
               "swift_plan_capture")
         return out
 
+    KERNEL_SLOTS = ("stats", "rows", "cols", "irows", "final", "fused")
+
+    def set_timing(self, enable: bool):
+        """Record CUDA events around every kernel of later forward calls."""
+        check(lib.swift_plan_set_timing(self._h, 1 if enable else 0), "swift_plan_set_timing")
+
+    def timings(self) -> dict:
+        """{kernel: (total ms, launches)} since the last read (synchronises)."""
+        ms = (C.c_float * 8)()
+        n = (C.c_int32 * 8)()
+        check(lib.swift_plan_timings(self._h, ms, n), "swift_plan_timings")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNEL_SLOTS) if n[i] > 0}
+
     def replay(self, stream=None):
         """Re-run the captured forward call with one graph launch."""
         check(lib.swift_plan_replay(self._h, _stream_ptr(stream)), "swift_plan_replay")

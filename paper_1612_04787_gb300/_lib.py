@@ -39,6 +39,8 @@ EXPORTS = (
     "swift_plan_autotune",
     "swift_plan_capture",
     "swift_plan_replay",
+    "swift_plan_set_timing",
+    "swift_plan_timings",
     "swift_status_string",
     "swift_version",
 )
@@ -98,6 +100,10 @@ def _load():
     lib.swift_plan_capture.restype = C.c_int
     lib.swift_plan_replay.argtypes = [C.c_void_p, C.c_void_p]
     lib.swift_plan_replay.restype = C.c_int
+    lib.swift_plan_set_timing.argtypes = [C.c_void_p, C.c_int32]
+    lib.swift_plan_set_timing.restype = C.c_int
+    lib.swift_plan_timings.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
+    lib.swift_plan_timings.restype = C.c_int
     lib.swift_status_string.argtypes = [C.c_int]
     lib.swift_status_string.restype = C.c_char_p
     lib.swift_version.argtypes = []

@@ -12,6 +12,7 @@
 namespace {
 
 constexpr int kMaxLevels = 8;
+constexpr int kTimingSets = 1024;
 constexpr int kSizes[3] = {64, 128, 256};
 
 int size_slot(int n) {
@@ -60,6 +61,12 @@ struct swift_plan_s {
   void* bwork = nullptr;
   long long bwork_windows = 0;
   double* gw_acc = nullptr;  // [kMaxLevels] accumulated dL/dw
+  // per-kernel timing (swift_plan_set_timing / swift_plan_timings): a ring
+  // of event sets, one set per streaming slice or fused launch
+  bool timing = false;
+  cudaEvent_t* tev = nullptr;   // [kTimingSets][6]
+  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch
+  int tcount = 0;               // sets used since the last read
   // one captured forward call (swift_plan_capture / swift_plan_replay)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -86,6 +93,11 @@ static swift_status release(swift_plan p) {
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
   if (p->work) cudaFree(p->work);
   if (p->bwork) cudaFree(p->bwork);
+  if (p->tev) {
+    for (int i = 0; i < 6 * kTimingSets; ++i) cudaEventDestroy(p->tev[i]);
+    delete[] p->tev;
+    delete[] p->tkind;
+  }
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->gw_acc) cudaFree(p->gw_acc);
@@ -227,7 +239,12 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
   if (plan->stream_level[l]) {
     for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
       const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
-      const swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
+      swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
+      if (plan->timing) {
+        const int set = plan->tcount++ % kTimingSets;
+        plan->tkind[set] = 0;
+        W.ev = plan->tev + 6 * set;
+      }
       if (swift::launch_stream(lv.n, plan->dtype, L, W, st) != cudaSuccess) return SWIFT_ERR_CUDA;
     }
     return SWIFT_OK;
@@ -236,7 +253,15 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
                     (reinterpret_cast<uintptr_t>(ri.data) % 16) == 0 &&
                     (reinterpret_cast<uintptr_t>(mi.data) % 16) == 0 && ri.pitch % 16 == 0 &&
                     mi.pitch % 16 == 0 && ri.width % 16 == 0 && mi.width % 16 == 0;
+  cudaEvent_t* ev = nullptr;
+  if (plan->timing) {
+    const int set = plan->tcount++ % kTimingSets;
+    plan->tkind[set] = 1;
+    ev = plan->tev + 6 * set;
+    cudaEventRecord(ev[0], st);
+  }
   if (swift::launch_forward(lv.n, plan->dtype, bulk, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+  if (ev) cudaEventRecord(ev[1], st);
   return SWIFT_OK;
 }
 
@@ -494,6 +519,59 @@ extern "C" swift_status swift_plan_replay(swift_plan plan, void* stream) {
     cudaGetLastError();
     return SWIFT_ERR_CUDA;
   }
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_timing(swift_plan plan, int32_t enable) {
+  if (!plan) return SWIFT_ERR_INVALID_ARG;
+  if (enable && !plan->tev) {
+    plan->tev = new (std::nothrow) cudaEvent_t[6 * kTimingSets];
+    plan->tkind = new (std::nothrow) int[kTimingSets];
+    if (!plan->tev || !plan->tkind) {
+      delete[] plan->tev;
+      delete[] plan->tkind;
+      plan->tev = nullptr;
+      plan->tkind = nullptr;
+      return SWIFT_ERR_OOM;
+    }
+    for (int i = 0; i < 6 * kTimingSets; ++i) {
+      if (cudaEventCreate(&plan->tev[i]) != cudaSuccess) {
+        for (int k = 0; k < i; ++k) cudaEventDestroy(plan->tev[k]);
+        delete[] plan->tev;
+        delete[] plan->tkind;
+        plan->tev = nullptr;
+        plan->tkind = nullptr;
+        cudaGetLastError();
+        return SWIFT_ERR_CUDA;
+      }
+    }
+  }
+  plan->timing = enable != 0;
+  plan->tcount = 0;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, int32_t* launches) {
+  if (!plan || !kernel_ms || !launches) return SWIFT_ERR_INVALID_ARG;
+  for (int k = 0; k < 8; ++k) {
+    kernel_ms[k] = 0.f;
+    launches[k] = 0;
+  }
+  if (!plan->tev) return SWIFT_OK;
+  const int used = plan->tcount < kTimingSets ? plan->tcount : kTimingSets;
+  for (int set = 0; set < used; ++set) {
+    cudaEvent_t* ev = plan->tev + 6 * set;
+    const int nk = plan->tkind[set] == 0 ? 5 : 1;
+    if (cudaEventSynchronize(ev[nk]) != cudaSuccess) return SWIFT_ERR_CUDA;
+    for (int k = 0; k < nk; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return SWIFT_ERR_CUDA;
+      const int slot = plan->tkind[set] == 0 ? k : 5;
+      kernel_ms[slot] += ms;
+      launches[slot] += 1;
+    }
+  }
+  plan->tcount = 0;
   return SWIFT_OK;
 }
 

@@ -38,6 +38,7 @@ struct StreamWork {
   unsigned long long* part;  // [S][blocks][3] block argmax key, FP64 sum of s, FP64 sum of s^2
   long long b0;              // first window of the slice
   long long count;           // windows in the slice
+  cudaEvent_t* ev = nullptr; // host: 6 events recorded around the five kernels (timing), or null
 };
 
 // streaming forward path (swim_stream.cu): bytes of workspace per window, launch of one slice

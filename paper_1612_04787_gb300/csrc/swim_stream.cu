@@ -35,11 +35,20 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
   if ((e = smem_optin(stream_rows_kernel<N, TIn>, rows_smem<N, TIn>(), m1, dev)) != cudaSuccess) return e;
   if ((e = smem_optin(stream_cols_kernel<N>, cols_smem<N>(), m2, dev)) != cudaSuccess) return e;
   if ((e = smem_optin(stream_irows_kernel<N>, irows_smem<N>(), m3, dev)) != cudaSuccess) return e;
+  auto mark = [&](int k) {
+    if (W.ev) cudaEventRecord(W.ev[k], st);
+  };
+  mark(0);
   stream_stats_kernel<N, TIn><<<S, 256, 0, st>>>(L, W);
+  mark(1);
   stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+  mark(2);
   stream_cols_kernel<N><<<S * G::NB2, 256, cols_smem<N>(), st>>>(L, W);
+  mark(3);
   stream_irows_kernel<N><<<S * G::NB3, 256, irows_smem<N>(), st>>>(L, W);
+  mark(4);
   stream_final_kernel<N><<<S, 32, 0, st>>>(L, W);
+  mark(5);
   return cudaGetLastError();
 }
 
