@@ -43,7 +43,7 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
   mark(1);
   stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
   mark(2);
-  stream_cols_kernel<N><<<S * G::NB2, 256, cols_smem<N>(), st>>>(L, W);
+  stream_cols_kernel<N><<<S * G::NB2, G::T2, cols_smem<N>(), st>>>(L, W);
   mark(3);
   stream_irows_kernel<N><<<S * G::NB3, 256, irows_smem<N>(), st>>>(L, W);
   mark(4);

@@ -39,8 +39,9 @@ struct StreamGeom {
   static constexpr int T = 256;
   static constexpr int RS = N == 256 ? 272 : (N == 128 ? 152 : 72);  // padded row stride
   static constexpr int RB = T / R2;        // K1: rows per CTA
-  static constexpr int CB = 128 / R2;      // K2: kx values (plus partners) per CTA
+  static constexpr int CB = 16;            // K2: kx values (plus partners) per CTA
   static constexpr int NB2 = N / (2 * CB);
+  static constexpr int T2 = 2 * CB * R2;   // K2: threads (one pass-A task each)
   static constexpr int PB = (T / R2) < (N / 2) ? (T / R2) : (N / 2);  // K3: row pairs per CTA
   static constexpr int NB3 = (N / 2) / PB;
   static_assert(R1 * R2 == N, "radix");
@@ -319,10 +320,10 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
 // SAVE: also store C = M conj(R) and R for kx in [0, n/2] (all ky) to `cr`
 // ([2][n][n/2+1]) for the backward pass.
 template <int N, bool SAVE = false>
-__global__ void __launch_bounds__(256) stream_cols_kernel(const MatchLaunch L, const StreamWork W,
-                                                          float2* cr = nullptr) {
+__global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const MatchLaunch L, const StreamWork W,
+                                                                        float2* cr = nullptr) {
   using G = StreamGeom<N>;
-  constexpr int R1 = G::R1, R2 = G::R2, CB = G::CB, T = G::T;
+  constexpr int R1 = G::R1, R2 = G::R2, CB = G::CB, T = G::T2;
   constexpr int LINES = 2 * CB;
   constexpr int LS = LINES + 8;  // padded row stride of the column slab
   const long long s = blockIdx.x / G::NB2;
