@@ -504,6 +504,19 @@ def dist_setup():
     return world, rank, local
 
 
+def aggregate_over_ranks(total_ms, windows, steps, world, device=None):
+    """Weak scaling: every rank runs the whole workload on its own GPU; the job
+    time is the slowest rank's (all-reduce MAX), and the value counts the
+    windows of all ranks.  Returns (job ms, windows/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * windows * steps / (total_ms / 1e3)
+
+
 def reference_arm(args):
     """The FP64 oracle timed on the host cores (no GPU)."""
     import synth
@@ -603,12 +616,7 @@ def main():
     if timing:
         W.plan.set_timing(False)
     durs = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    total_ms = sum(durs)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * W.windows * args.steps / (total_ms / 1e3)
+    total_ms, value = aggregate_over_ranks(sum(durs), W.windows, args.steps, world, dev)
     print(f"[bench] {W.name} rank {rank}: {args.steps} steps, {total_ms / args.steps:.4f} ms/step, "
           f"{value:.1f} windows/s", file=sys.stderr, flush=True)
 
