@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <new>
+#include <vector>
 #include <stdint.h>
 #include <string.h>
 
@@ -53,6 +54,8 @@ struct swift_plan_s {
   float* taper[kMaxLevels] = {};
   double inv_sum_a[kMaxLevels] = {};
   float2* twiddle[3] = {};
+  // tensor-core precision variant: DFT block matrices per window size
+  float* tc_mats[3] = {};
   // streaming forward path: per-level choice and its workspace
   int stream_level[kMaxLevels] = {};
   void* work = nullptr;
@@ -65,7 +68,7 @@ struct swift_plan_s {
   // of event sets, one set per streaming slice or fused launch
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // [kTimingSets][6]
-  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch
+  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch, 2 = tensor-core set
   int tcount = 0;               // sets used since the last read
   // one captured forward call (swift_plan_capture / swift_plan_replay)
   cudaGraph_t graph = nullptr;
@@ -89,8 +92,10 @@ static swift_status release(swift_plan p) {
   if (cur != p->device) cudaSetDevice(p->device);
   for (int l = 0; l < kMaxLevels; ++l)
     if (p->taper[l]) cudaFree(p->taper[l]);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 3; ++i) {
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
+    if (p->tc_mats[i]) cudaFree(p->tc_mats[i]);
+  }
   if (p->work) cudaFree(p->work);
   if (p->bwork) cudaFree(p->bwork);
   if (p->tev) {
@@ -112,9 +117,10 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
   if (!out || !levels || n_levels < 1 || n_levels > kMaxLevels || max_windows <= 0) return SWIFT_ERR_INVALID_ARG;
   if (in != SWIFT_IN_U8 && in != SWIFT_IN_F32) return SWIFT_ERR_INVALID_ARG;
   if (prec != SWIFT_PREC_FP32 && prec != SWIFT_PREC_BF16X2 && prec != SWIFT_PREC_FP16X2) return SWIFT_ERR_INVALID_ARG;
-  if (prec != SWIFT_PREC_FP32) return SWIFT_ERR_UNSUPPORTED;
   for (int l = 0; l < n_levels; ++l) {
     const swift_level& lv = levels[l];
+    // the tensor-core variant is built for 128 x 128 and 256 x 256 windows
+    if (prec != SWIFT_PREC_FP32 && lv.n != 128 && lv.n != 256) return SWIFT_ERR_UNSUPPORTED;
     if (lv.n < 2 || (lv.n & (lv.n - 1)) != 0) return SWIFT_ERR_INVALID_ARG;
     if (!(lv.whiten_exponent >= 0.f && lv.whiten_exponent <= 1.f)) return SWIFT_ERR_INVALID_ARG;
     if (lv.apod != SWIFT_APOD_NONE && lv.apod != SWIFT_APOD_HANN && lv.apod != SWIFT_APOD_TUKEY)
@@ -170,14 +176,29 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
         return SWIFT_ERR_OOM;
       }
     }
+    if (prec != SWIFT_PREC_FP32 && !p->tc_mats[slot]) {
+      const size_t nf = swift::tc_matrix_floats(n);
+      std::vector<float> m(nf);
+      swift::tc_build_matrices(n, m.data());
+      if (cudaMalloc(&p->tc_mats[slot], sizeof(float) * nf) != cudaSuccess ||
+          cudaMemcpy(p->tc_mats[slot], m.data(), sizeof(float) * nf, cudaMemcpyHostToDevice) != cudaSuccess) {
+        release(p);
+        cudaGetLastError();
+        return SWIFT_ERR_OOM;
+      }
+    }
   }
-  // workspace of the streaming forward path
+  // workspace of the streaming forward path (and of the tensor-core variant)
   // sized for the largest level, so any level can be switched to streaming
   size_t per = 0;
   for (int l = 0; l < n_levels; ++l) {
     p->stream_level[l] = default_stream(levels[l].n) ? 1 : 0;
     const size_t b = swift::stream_bytes_per_window(levels[l].n);
     per = b > per ? b : per;
+    if (prec != SWIFT_PREC_FP32) {
+      const size_t t = swift::tc_bytes_per_window(levels[l].n);
+      per = t > per ? t : per;
+    }
   }
   if (per > 0) {
     p->work_windows = max_windows < kStreamSlice ? max_windows : kStreamSlice;
@@ -236,6 +257,22 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
   L.taper = plan->taper[l];
   L.twiddle = plan->twiddle[size_slot(lv.n)];
   L.out = out;
+  if (plan->prec != SWIFT_PREC_FP32) {
+    const bool fp16 = plan->prec == SWIFT_PREC_FP16X2;
+    for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
+      const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
+      swift::StreamWork W;
+      const swift::TcLaunch T =
+          swift::tc_carve(plan->work, plan->work_windows, lv.n, plan->tc_mats[size_slot(lv.n)], b0, cnt, &W);
+      if (plan->timing) {
+        const int set = plan->tcount++ % kTimingSets;
+        plan->tkind[set] = 2;
+        W.ev = plan->tev + 6 * set;
+      }
+      if (swift::launch_tc(lv.n, plan->dtype, fp16, L, W, T, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+    }
+    return SWIFT_OK;
+  }
   if (plan->stream_level[l]) {
     for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
       const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
@@ -361,6 +398,7 @@ static swift_status ensure_bwork(swift_plan plan) {
 // validation shared by the warp forward and the backward (section mode)
 static swift_status check_warp_batch(swift_plan plan, const swift_batch* batch) {
   if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
+  if (plan->prec != SWIFT_PREC_FP32) return SWIFT_ERR_UNSUPPORTED;  // warp / backward are FP32 only
   const int64_t B = batch->n_windows;
   if (B < 0 || B > plan->max_windows) return SWIFT_ERR_INVALID_ARG;
   if (B == 0) return SWIFT_OK;
@@ -561,14 +599,17 @@ extern "C" swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, in
   const int used = plan->tcount < kTimingSets ? plan->tcount : kTimingSets;
   for (int set = 0; set < used; ++set) {
     cudaEvent_t* ev = plan->tev + 6 * set;
-    const int nk = plan->tkind[set] == 0 ? 5 : 1;
+    const int kind = plan->tkind[set];
+    const int nk = kind == 1 ? 1 : 5;
     if (cudaEventSynchronize(ev[nk]) != cudaSuccess) return SWIFT_ERR_CUDA;
+    // tensor-core sets: statistics, GEMMs (forward), whitening, GEMMs (inverse), reduce + finalize
+    static const int tc_slot[5] = {0, 6, 7, 6, 4};
     for (int k = 0; k < nk; ++k) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return SWIFT_ERR_CUDA;
-      const int slot = plan->tkind[set] == 0 ? k : 5;
+      const int slot = kind == 0 ? k : (kind == 1 ? 5 : tc_slot[k]);
       kernel_ms[slot] += ms;
-      launches[slot] += 1;
+      launches[slot] += (kind == 2 && k == 3) ? 0 : 1;
     }
   }
   plan->tcount = 0;
