@@ -52,13 +52,15 @@ typedef enum { SWIFT_APOD_NONE = 0, SWIFT_APOD_HANN = 1, SWIFT_APOD_TUKEY = 2 } 
 typedef enum { SWIFT_IN_U8 = 0, SWIFT_IN_F32 = 1 } swift_dtype;
 
 /* Arithmetic of the transforms.  FP32 is the plain form (radix-16/8
- * butterflies on the FP32 units).  BF16X2 and FP16X2 run every 1D DFT as a
- * dense DFT-matrix GEMM on the tensor cores: operands split into hi + lo
- * 16-bit parts, products hi*hi + hi*lo + lo*hi accumulated in FP32 (FP16X2
- * scales each operand slab by a power of two to stay in FP16's range).
- * Statistics, SNR and the subpixel fit are the FP32 form's FP64-accumulated
- * kernels in every precision.  BF16X2 / FP16X2 support window sizes 128 and
- * 256 and the plain (unwarped) forward only. */
+ * butterflies on the FP32 units).  BF16X2 and FP16X2 compute every 1D DFT
+ * on the tensor cores, one warp per transform, by the four-step
+ * factorisation n = 16 x (n/16): both small DFTs are mma.sync products with
+ * operands split into hi + lo 16-bit parts (products hi*hi + hi*lo + lo*hi,
+ * FP32 accumulation) and FP32 twiddles between them (FP16X2 scales each
+ * transform's input by a power of two to stay in FP16's range).  Statistics,
+ * SNR and the subpixel fit are the FP32 form's FP64-accumulated kernels in
+ * every precision.  BF16X2 / FP16X2 support window sizes 128 and 256 and the
+ * plain (unwarped) forward only. */
 typedef enum { SWIFT_PREC_FP32 = 0, SWIFT_PREC_BF16X2 = 1, SWIFT_PREC_FP16X2 = 2 } swift_precision;
 
 /* Per-window status codes (swift_result.status). */
@@ -262,10 +264,9 @@ swift_status swift_plan_replay(swift_plan plan, void* stream);
  * summed device time in ms and the number of launches since the last read,
  * then starts over.  Slots: 0 statistics, 1 row transforms, 2 column
  * transforms + whitening, 3 inverse row transforms, 4 finalize (the
- * streaming schedule; under BF16X2 / FP16X2 slot 4 holds the response
- * reduction + finalize), 5 fused kernel, 6 tensor-core GEMMs (forward and
- * inverse, one launch record per slice), 7 tensor-core unpack + whitening.
- * kernel_ms and launches are host arrays of 8. */
+ * streaming schedule, and the same five kernels of the BF16X2 / FP16X2
+ * forms), 5 fused kernel, 6-7 unused.  kernel_ms and launches are host
+ * arrays of 8. */
 swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
 swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, int32_t* launches);
 

@@ -167,7 +167,7 @@ class Plan:
               "swift_plan_capture")
         return out
 
-    KERNEL_SLOTS = ("stats", "rows", "cols", "irows", "final", "fused", "tc_gemm", "tc_whiten")
+    KERNEL_SLOTS = ("stats", "rows", "cols", "irows", "final", "fused")
 
     def set_timing(self, enable: bool):
         """Record CUDA events around every kernel of later forward calls."""

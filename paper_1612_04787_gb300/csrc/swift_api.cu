@@ -3,7 +3,6 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <new>
-#include <vector>
 #include <stdint.h>
 #include <string.h>
 
@@ -54,8 +53,8 @@ struct swift_plan_s {
   float* taper[kMaxLevels] = {};
   double inv_sum_a[kMaxLevels] = {};
   float2* twiddle[3] = {};
-  // tensor-core precision variant: DFT block matrices per window size
-  float* tc_mats[3] = {};
+  // tensor-core precision variant: fragment and twiddle tables per window size
+  void* tc_tab[3] = {};
   // streaming forward path: per-level choice and its workspace
   int stream_level[kMaxLevels] = {};
   void* work = nullptr;
@@ -68,7 +67,7 @@ struct swift_plan_s {
   // of event sets, one set per streaming slice or fused launch
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // [kTimingSets][6]
-  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch, 2 = tensor-core set
+  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch
   int tcount = 0;               // sets used since the last read
   // one captured forward call (swift_plan_capture / swift_plan_replay)
   cudaGraph_t graph = nullptr;
@@ -94,7 +93,7 @@ static swift_status release(swift_plan p) {
     if (p->taper[l]) cudaFree(p->taper[l]);
   for (int i = 0; i < 3; ++i) {
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
-    if (p->tc_mats[i]) cudaFree(p->tc_mats[i]);
+    if (p->tc_tab[i]) cudaFree(p->tc_tab[i]);
   }
   if (p->work) cudaFree(p->work);
   if (p->bwork) cudaFree(p->bwork);
@@ -176,29 +175,22 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
         return SWIFT_ERR_OOM;
       }
     }
-    if (prec != SWIFT_PREC_FP32 && !p->tc_mats[slot]) {
-      const size_t nf = swift::tc_matrix_floats(n);
-      std::vector<float> m(nf);
-      swift::tc_build_matrices(n, m.data());
-      if (cudaMalloc(&p->tc_mats[slot], sizeof(float) * nf) != cudaSuccess ||
-          cudaMemcpy(p->tc_mats[slot], m.data(), sizeof(float) * nf, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (prec != SWIFT_PREC_FP32 && !p->tc_tab[slot]) {
+      if (cudaMalloc(&p->tc_tab[slot], swift::tcf_table_bytes(n)) != cudaSuccess ||
+          swift::tcf_build_tables(n, prec == SWIFT_PREC_FP16X2, p->tc_tab[slot]) != cudaSuccess) {
         release(p);
         cudaGetLastError();
         return SWIFT_ERR_OOM;
       }
     }
   }
-  // workspace of the streaming forward path (and of the tensor-core variant)
+  // workspace of the streaming forward path (also used by the tensor-core variant)
   // sized for the largest level, so any level can be switched to streaming
   size_t per = 0;
   for (int l = 0; l < n_levels; ++l) {
     p->stream_level[l] = default_stream(levels[l].n) ? 1 : 0;
     const size_t b = swift::stream_bytes_per_window(levels[l].n);
     per = b > per ? b : per;
-    if (prec != SWIFT_PREC_FP32) {
-      const size_t t = swift::tc_bytes_per_window(levels[l].n);
-      per = t > per ? t : per;
-    }
   }
   if (per > 0) {
     p->work_windows = max_windows < kStreamSlice ? max_windows : kStreamSlice;
@@ -261,15 +253,14 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
     const bool fp16 = plan->prec == SWIFT_PREC_FP16X2;
     for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
       const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
-      swift::StreamWork W;
-      const swift::TcLaunch T =
-          swift::tc_carve(plan->work, plan->work_windows, lv.n, plan->tc_mats[size_slot(lv.n)], b0, cnt, &W);
+      swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
       if (plan->timing) {
         const int set = plan->tcount++ % kTimingSets;
-        plan->tkind[set] = 2;
+        plan->tkind[set] = 0;
         W.ev = plan->tev + 6 * set;
       }
-      if (swift::launch_tc(lv.n, plan->dtype, fp16, L, W, T, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+      const swift::TcfLaunch T = swift::tcf_tables(plan->tc_tab[size_slot(lv.n)]);
+      if (swift::launch_tcf(lv.n, plan->dtype, fp16, L, W, T, st) != cudaSuccess) return SWIFT_ERR_CUDA;
     }
     return SWIFT_OK;
   }
@@ -599,17 +590,14 @@ extern "C" swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, in
   const int used = plan->tcount < kTimingSets ? plan->tcount : kTimingSets;
   for (int set = 0; set < used; ++set) {
     cudaEvent_t* ev = plan->tev + 6 * set;
-    const int kind = plan->tkind[set];
-    const int nk = kind == 1 ? 1 : 5;
+    const int nk = plan->tkind[set] == 0 ? 5 : 1;
     if (cudaEventSynchronize(ev[nk]) != cudaSuccess) return SWIFT_ERR_CUDA;
-    // tensor-core sets: statistics, GEMMs (forward), whitening, GEMMs (inverse), reduce + finalize
-    static const int tc_slot[5] = {0, 6, 7, 6, 4};
     for (int k = 0; k < nk; ++k) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return SWIFT_ERR_CUDA;
-      const int slot = kind == 0 ? k : (kind == 1 ? 5 : tc_slot[k]);
+      const int slot = plan->tkind[set] == 0 ? k : 5;
       kernel_ms[slot] += ms;
-      launches[slot] += (kind == 2 && k == 3) ? 0 : 1;
+      launches[slot] += 1;
     }
   }
   plan->tcount = 0;

@@ -83,22 +83,17 @@ cudaError_t launch_prepared_forward(int n, const MatchLaunch& L, const BackWork&
 cudaError_t launch_backward(int n, swift_dtype dtype, const MatchLaunch& L, const BackLaunch& K, const BackWork& BW,
                             long long b0, cudaStream_t stream);
 
-// tensor-core precision variant (swim_tc.cu)
-struct TcLaunch {
-  const float* mats;  // [4][2n][2n] DFT block matrices: Wr, Wc, Wri (2n x n), Wci
-  float* x0;          // [S][2][n][n] planar buffer
-  float* x1;          // [S][2][n][n] planar buffer
-  float4* stats;      // [S] window statistics
-  long long b0;       // first window of the slice
-  long long count;    // windows in the slice
+// tensor-core precision variant (swim_tcf.cu): tables per window size, and
+// the five-kernel schedule on the streaming workspace
+struct TcfLaunch {
+  const uint32_t* frag;  // [32][40] per-lane constant DFT fragments (hi / lo)
+  const float2* tw;      // [n] W_n^m = exp(-2 pi i m / n)
 };
-size_t tc_bytes_per_window(int n);
-size_t tc_matrix_floats(int n);
-void tc_build_matrices(int n, float* m);
-TcLaunch tc_carve(void* base, long long capacity, int n, const float* mats, long long b0, long long count,
-                  StreamWork* W);
-cudaError_t launch_tc(int n, swift_dtype dtype, bool fp16, const MatchLaunch& L, const StreamWork& W,
-                      const TcLaunch& T, cudaStream_t stream);
+size_t tcf_table_bytes(int n);
+cudaError_t tcf_build_tables(int n, bool fp16, void* dst);
+TcfLaunch tcf_tables(const void* dst);
+cudaError_t launch_tcf(int n, swift_dtype dtype, bool fp16, const MatchLaunch& L, const StreamWork& W,
+                       const TcfLaunch& T, cudaStream_t stream);
 
 // float32 copy of the accumulated dL/dw of n levels
 cudaError_t launch_wout(const double* acc, float* out, int n, cudaStream_t stream);
