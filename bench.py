@@ -70,6 +70,91 @@ def fp32_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
     return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
+def tensor_flops(n: int) -> dict:
+    """Executed tensor-core work of the BF16X2 / FP16X2 kernels per window: a
+    warp's n-point DFT issues 16 (n = 256) or 6 (n = 128) m16n8k16 products per
+    hi/lo term, three terms; rows transform n lines, columns 3 per kx pair
+    (n/2 pairs), inverse rows n/2 packed lines."""
+    per_dft = 2 * 16 * 8 * 16 * (48 if n == 256 else 18)
+    return {"rows": n * per_dft, "cols": (3 * n // 2) * per_dft, "irows": (n // 2) * per_dft,
+            "stats": 0.0, "final": 0.0}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------------------------- #
+# library comparisons: the same match on cuFFT (torch.fft) and on host FFTs
+# --------------------------------------------------------------------------- #
+def fft_match_torch(torch, mov, ref, A, w):
+    """Apodise, rfft2, C = M conj(R), whitening, irfft2, argmax: the transform
+    part of the match with library FFTs (no SNR or subpixel fit)."""
+    n = mov.shape[-1]
+    sa = A.sum()
+    mp = A * (mov - (A * mov).sum((-2, -1), keepdim=True) / sa)
+    rp = A * (ref - (A * ref).sum((-2, -1), keepdim=True) / sa)
+    c = torch.fft.rfft2(mp) * torch.fft.rfft2(rp).conj()
+    mag2 = c.real * c.real + c.imag * c.imag
+    g = c * (torch.where(mag2 > 0, mag2.pow(-0.5 * w), torch.zeros_like(mag2)) / (n * n))
+    g[:, 0, 0] = 0
+    return torch.fft.irfft2(g, s=(n, n)).flatten(1).argmax(1)
+
+
+def cufft_throughput(torch, W, stream, steps, flush):
+    """Windows/s of the library-FFT match (cuFFT through torch.fft), window
+    gather included, with the same L2 flush between steps."""
+    get = W.torch_windows(torch)
+    A = torch.outer(*(2 * [0.5 - 0.5 * torch.cos(2 * math.pi * torch.arange(W.n, device=flush.device,
+                                                                         dtype=torch.float32) / W.n)]))
+    for _ in range(3):
+        for m, r in get():
+            fft_match_torch(torch, m, r, A, W.w)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        for m, r in get():
+            fft_match_torch(torch, m, r, A, W.w)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return W.windows / (ms / 1e3), ms
+
+
+def cpu_fft_throughput(movs, refs, n, w):
+    """Windows/s of the same library-FFT match in float32 on the host cores
+    (scipy.fft, all cores): the like-for-like counterpart of single-precision
+    FFTW on CPU cores."""
+    import scipy.fft as sf
+    cores = len(os.sched_getaffinity(0))
+    a = (0.5 - 0.5 * np.cos(2 * np.pi * np.arange(n) / n)).astype(np.float32)
+    A = np.outer(a, a)
+    m = np.stack(movs).astype(np.float32)
+    r = np.stack(refs).astype(np.float32)
+
+    def run():
+        sa = A.sum()
+        mp = A * (m - (A * m).sum((1, 2), keepdims=True) / sa)
+        rp = A * (r - (A * r).sum((1, 2), keepdims=True) / sa)
+        c = sf.rfft2(mp, workers=cores) * np.conj(sf.rfft2(rp, workers=cores))
+        mag2 = (c.real * c.real + c.imag * c.imag).astype(np.float32)
+        with np.errstate(divide="ignore"):
+            g = c * (np.where(mag2 > 0, mag2 ** np.float32(-0.5 * w), 0).astype(np.float32) / (n * n))
+        g[:, 0, 0] = 0
+        return sf.irfft2(g, s=(n, n), workers=cores).reshape(len(m), -1).argmax(1)
+
+    run()
+    t0 = time.perf_counter()
+    run()
+    dt = time.perf_counter() - t0
+    return len(m) / dt, cores, dt
+
+
 # --------------------------------------------------------------------------- #
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------- #
@@ -234,6 +319,16 @@ class Sections:
 
     def ok_fraction(self, swift):
         return float((swift.decode(self.outs[0])["status"] == 0).mean())
+
+    def torch_windows(self, torch):
+        n, st = self.n, self.stride
+
+        def get():
+            for a, b in self.d:
+                mw = b.unfold(0, n, st).unfold(1, n, st).reshape(-1, n, n)[:self.B1].float()
+                rw = a.unfold(0, n, st).unfold(1, n, st).reshape(-1, n, n)[:self.B1].float()
+                yield mw, rw
+        return get
 
     def oracle_windows(self, k):
         a, b = self.secs[0]
@@ -414,6 +509,11 @@ class Patches:
     def ok_fraction(self, swift):
         return float((swift.decode(self.out)["status"] == 0).mean())
 
+    def torch_windows(self, torch):
+        def get():
+            yield self.mov, self.ref
+        return get
+
     def oracle_windows(self, k):
         r = self.ref[:k].double().cpu().numpy()
         m = self.mov[:k].double().cpu().numpy()
@@ -549,6 +649,8 @@ def reference_arm(args):
 
 KERNEL_NAMES = {"stats": "stream_stats_kernel", "rows": "stream_rows_kernel", "cols": "stream_cols_kernel",
                 "irows": "stream_irows_kernel", "final": "stream_final_kernel", "fused": "swim_forward_kernel"}
+TC_KERNEL_NAMES = {"stats": "stream_stats_kernel", "rows": "tcf_rows_kernel", "cols": "tcf_cols_kernel",
+                   "irows": "tcf_irows_kernel", "final": "stream_final_kernel"}
 
 
 def main():
@@ -564,6 +666,7 @@ def main():
     ap.add_argument("--windows", type=int, default=0, help="limit the windows per step (small profiling cases)")
     ap.add_argument("--oracle-sample", type=int, default=961)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the cuFFT and host-FFT comparisons")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -630,14 +733,28 @@ def main():
     e2e_value = world * W.windows * e2e_steps / e2e_s
     h2d, d2h = W.io_bytes()
 
-    cpu = None
+    cufft = None
+    if hasattr(W, "torch_windows") and not args.no_compare:
+        v, ms = cufft_throughput(torch, W, stream, min(args.steps, 20), flush)
+        cufft = {"value": v, "unit": "windows/s", "ms_per_step": ms,
+                 "kind": "cuFFT through torch.fft: apodise, rfft2, C = M conj(R), whitening, irfft2, argmax "
+                         "(window gather included; no SNR or subpixel fit); a library comparison, not the product"}
+
+    cpu = cpu_fft = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         movs, refs, n, w, r = W.oracle_windows(args.oracle_sample)
         v, cores, dt = oracle_throughput(movs, refs, n, w, r)
         cpu = {"value": v, "unit": "windows/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(movs)} windows of the workload ({n}x{n}), FP64 direct-DFT oracle, forward only, "
                          f"one single-threaded process per core ({dt:.1f} s)"}
+        if not args.no_compare:
+            v, cores, dt = cpu_fft_throughput(movs, refs, n, w)
+            cpu_fft = {"value": v, "unit": "windows/s", "cores": cores,
+                       "kind": "scipy.fft float32 (pocketfft), all host cores: apodise, rfft2, C = M conj(R), "
+                               "whitening, irfft2, argmax (no SNR or subpixel fit)",
+                       "sample": f"{len(movs)} windows of the workload ({n}x{n}), {dt:.2f} s"}
 
+    tensor = args.precision != "fp32"
     peak = fp32_peak_tflops()
     step_tflops = W.flops / (total_ms / args.steps / 1e3) / 1e12
     if kt:
@@ -645,26 +762,41 @@ def main():
         launches = kt[dom][1]
         dom_ms = kt[dom][0] / launches
         windows_per_launch = W.windows * args.steps / launches
-        achieved = kernel_flops(W.dominant_n)[dom] * windows_per_launch / (dom_ms / 1e3) / 1e12
+        per_window = tensor_flops(W.dominant_n)[dom] if tensor else kernel_flops(W.dominant_n)[dom]
+        achieved = per_window * windows_per_launch / (dom_ms / 1e3) / 1e12
         tot = sum(x[0] for x in kt.values())
         shares = {k: round(v[0] / tot, 4) for k, v in kt.items()}
-        dom_name = KERNEL_NAMES[dom]
+        dom_name = (TC_KERNEL_NAMES if tensor else KERNEL_NAMES)[dom]
     else:
         dom_name, achieved, shares, windows_per_launch = "pipeline (graph replay)", step_tflops, None, W.windows
     traffic = recorded_traffic(f"{dom_name}<{W.dominant_n}>", windows_per_launch)
+    if tensor:
+        pk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                    "traffic": traffic, "kernel": f"{dom_name}<{W.dominant_n}>",
+                    "peak_note": "measured dense BF16 cuBLAS GEMM, sustained (MEASURED_PEAKS.json); FP16 has the "
+                                 "same nominal rate; achieved counts the executed m16n8k16 products (three hi/lo "
+                                 "terms), not algorithmic FFT work; mma.sync m16n8k16 itself measured ~600 TFLOP/s "
+                                 "on this GPU",
+                    "kernel_share_of_step": shares,
+                    "algorithmic_fp32_tflops": step_tflops, "algorithmic_fp32_frac": step_tflops / peak}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": f"{dom_name}<{W.dominant_n}>",
+                    "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
+                    "kernel_share_of_step": shares,
+                    "pipeline_tflops": step_tflops, "pipeline_frac": step_tflops / peak}
     line = {
         "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world, "steps": args.steps,
         "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x2": "bf16x2 (f32 accumulate)",
+                                                         "fp16x2": "f16x2 (f32 accumulate)"}[args.precision],
+        "data": "synthetic",
         "config": dict({"workload": W.description, "name": W.name,
                         "l2": "flushed before every timed step (256 MiB write, outside the step's events)",
                         "status_ok_fraction": ok_frac}, **W.config),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"{dom_name}<{W.dominant_n}>",
-                     "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
-                     "kernel_share_of_step": shares,
-                     "pipeline_tflops": step_tflops, "pipeline_frac": step_tflops / peak},
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "windows/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": args.steps * W.launches_per_step,
@@ -672,6 +804,10 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if cpu_fft is not None:
+        line["cpu_fft_baseline"] = cpu_fft
+    if cufft is not None:
+        line["cufft_comparison"] = cufft
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
