@@ -33,6 +33,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -166,7 +167,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: SWIFT_CLOCKS_DIR if set (kept for inspection), else a temporary directory
+        d = os.environ.get("SWIFT_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"swift_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:

@@ -122,10 +122,25 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
                                          static_cast<uintptr_t>(mpitch * sizeof(TIn)) |
                                          static_cast<uintptr_t>(rpitch * sizeof(TIn))) & 15) == 0;
   if (vec) {
-    for (int e = tid; e < N * N / VEC; e += 256) {
+    // batches of BATCH vectors per thread and image, all loads issued before use
+    constexpr int PER = N * N / VEC / 256;
+    constexpr int BATCH = PER < 8 ? PER : 8;
+    static_assert(PER % BATCH == 0, "vector batches");
+#pragma unroll 1
+    for (int i0 = 0; i0 < PER; i0 += BATCH) {
+      uint4 mqs[BATCH], rqs[BATCH];
+#pragma unroll
+      for (int bq = 0; bq < BATCH; ++bq) {
+        const int e = tid + (i0 + bq) * 256;
+        const int y = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
+        mqs[bq] = __ldg(reinterpret_cast<const uint4*>(mbase + y * mpitch + x0));
+        rqs[bq] = __ldg(reinterpret_cast<const uint4*>(rbase + y * rpitch + x0));
+      }
+#pragma unroll
+      for (int bq = 0; bq < BATCH; ++bq) {
+      const int e = tid + (i0 + bq) * 256;
       const int y = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
-      const uint4 mq = __ldg(reinterpret_cast<const uint4*>(mbase + y * mpitch + x0));
-      const uint4 rq = __ldg(reinterpret_cast<const uint4*>(rbase + y * rpitch + x0));
+      const uint4 mq = mqs[bq], rq = rqs[bq];
       const float ay = tap[y];
       if constexpr (sizeof(TIn) == 1) {
         const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w}, rw[4] = {rq.x, rq.y, rq.z, rq.w};
@@ -142,6 +157,7 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
                              __uint_as_float(rq.w)};
 #pragma unroll
         for (int k = 0; k < 4; ++k) accum(ay * tap[x0 + k], mf[k], rf[k]);
+      }
       }
     }
   } else {
@@ -332,8 +348,7 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
   if (stat_status(W.stats[s]) != SWIFT_WIN_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [ky][lc], row stride LS
-  float2* dcbuf = slab + N * LS;
-  float2* twid = dcbuf + N;
+  float2* twid = slab + N * LS;
   for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
   // gather columns kx(lc) of Zr (rows are contiguous in kx)
   const float2* zr = W.zr + s * N * N;
@@ -380,62 +395,75 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
     for (int k2 = 0; k2 < R2; ++k2) slab[(R2 * k1 + k2) * LS + lc] = v[k2];
   }
   __syncthreads();
-  // unpack + whiten + inverse pass B' on lc < CB (kx = CB*cb + lc)
+  // unpack + whiten on lines lc < CB (kx = CB*cb + lc), all threads: slab row
+  // p = R2 k1 + k2 holds ky = k1 + R1 k2; the partner Z[-ky][-kx] sits in line
+  // lc + CB (line 0 of block 0 is its own partner and carries kx = n/2 in
+  // line CB).  G is written in place after every read is done.
   const float half_w = -0.5f * L.w;
   const float inv_n2 = 1.0f / (static_cast<float>(N) * static_cast<float>(N));
+  constexpr int EW = N * CB / T;  // elements per thread
+  static_assert(EW * T == N * CB, "whitening split");
+  float2 gv[EW];
+#pragma unroll
+  for (int i = 0; i < EW; ++i) {
+    const int e = tid + i * T;
+    const int p = e / CB, lc = e % CB;
+    const int ky = p / R2 + R1 * (p % R2);
+    const int nky = (N - ky) & (N - 1);
+    const bool dc_col = (cb == 0 && lc == 0);
+    const int plc = dc_col ? 0 : lc + CB;
+    const float2 a = slab[p * LS + lc];
+    const float2 bb = slab[G::rho(nky) * LS + plc];
+    const float2 c = make_float2(0.5f * fmaf(a.x, bb.y, a.y * bb.x),
+                                 0.25f * ((a.x * a.x + a.y * a.y) - (bb.x * bb.x + bb.y * bb.y)));
+    const float mag2 = fmaf(c.x, c.x, c.y * c.y);
+    const float sc = mag2 > 0.f ? exp2f(half_w * log2f(mag2)) * inv_n2 : 0.f;
+    float2 g = make_float2(c.x * sc, c.y * sc);
+    if constexpr (SAVE) {
+      // R = (A - conj(B)) / 2i
+      const size_t o = (static_cast<size_t>(s) * 2 * N + ky) * (N / 2 + 1) + (CB * cb + lc);
+      cr[o] = c;
+      cr[o + static_cast<size_t>(N) * (N / 2 + 1)] = make_float2(0.5f * (a.y + bb.y), -0.5f * (a.x - bb.x));
+    }
+    if (dc_col) {
+      const float2 a2 = slab[p * LS + CB];
+      const float2 b2 = slab[G::rho(nky) * LS + CB];
+      const float2 c2 = make_float2(0.5f * fmaf(a2.x, b2.y, a2.y * b2.x),
+                                    0.25f * ((a2.x * a2.x + a2.y * a2.y) - (b2.x * b2.x + b2.y * b2.y)));
+      if constexpr (SAVE) {
+        const size_t o = (static_cast<size_t>(s) * 2 * N + ky) * (N / 2 + 1) + N / 2;
+        cr[o] = c2;
+        cr[o + static_cast<size_t>(N) * (N / 2 + 1)] = make_float2(0.5f * (a2.y + b2.y), -0.5f * (a2.x - b2.x));
+      }
+      const float mq = fmaf(c2.x, c2.x, c2.y * c2.y);
+      const float sq = mq > 0.f ? exp2f(half_w * log2f(mq)) * inv_n2 : 0.f;
+      if (ky == 0) g = make_float2(0.f, 0.f);  // G[0,0] = 0
+      g = make_float2(g.x - c2.y * sq, g.y + c2.x * sq);
+    }
+    gv[i] = g;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < EW; ++i) {
+    const int e = tid + i * T;
+    slab[(e / CB) * LS + e % CB] = gv[i];
+  }
+  __syncthreads();
+  // inverse pass B' on lines lc < CB, in place
   constexpr int TBh = CB * R1, TAh = CB * R2;
 #pragma unroll
   for (int i = 0; i < (TBh + T - 1) / T; ++i) {
     const int task = tid + i * T;
     if (TBh % T != 0 && task >= TBh) break;
     const int k1 = task / CB, lc = task % CB;
-    const bool dc_col = (cb == 0 && lc == 0);
-    const int plc = dc_col ? 0 : lc + CB;
     float2 v[R2];
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) {
-      const int ky = k1 + R1 * k2;
-      const int nky = (N - ky) & (N - 1);
-      const float2 a = slab[(R2 * k1 + k2) * LS + lc];
-      const float2 bb = slab[G::rho(nky) * LS + plc];
-      const float2 c = make_float2(0.5f * fmaf(a.x, bb.y, a.y * bb.x),
-                                   0.25f * ((a.x * a.x + a.y * a.y) - (bb.x * bb.x + bb.y * bb.y)));
-      const float mag2 = fmaf(c.x, c.x, c.y * c.y);
-      const float sc = mag2 > 0.f ? exp2f(half_w * log2f(mag2)) * inv_n2 : 0.f;
-      float2 g = make_float2(c.x * sc, c.y * sc);
-      if constexpr (SAVE) {
-        // R = (A - conj(B)) / 2i
-        const size_t o = (static_cast<size_t>(s) * 2 * N + ky) * (N / 2 + 1) + (CB * cb + lc);
-        cr[o] = c;
-        cr[o + static_cast<size_t>(N) * (N / 2 + 1)] = make_float2(0.5f * (a.y + bb.y), -0.5f * (a.x - bb.x));
-      }
-      if (dc_col) {
-        const float2 a2 = slab[(R2 * k1 + k2) * LS + CB];
-        const float2 b2 = slab[G::rho(nky) * LS + CB];
-        const float2 c2 = make_float2(0.5f * fmaf(a2.x, b2.y, a2.y * b2.x),
-                                      0.25f * ((a2.x * a2.x + a2.y * a2.y) - (b2.x * b2.x + b2.y * b2.y)));
-        if constexpr (SAVE) {
-          const size_t o = (static_cast<size_t>(s) * 2 * N + ky) * (N / 2 + 1) + N / 2;
-          cr[o] = c2;
-          cr[o + static_cast<size_t>(N) * (N / 2 + 1)] = make_float2(0.5f * (a2.y + b2.y), -0.5f * (a2.x - b2.x));
-        }
-        const float mq = fmaf(c2.x, c2.x, c2.y * c2.y);
-        const float sq = mq > 0.f ? exp2f(half_w * log2f(mq)) * inv_n2 : 0.f;
-        if (ky == 0) g = make_float2(0.f, 0.f);  // G[0,0] = 0
-        g = make_float2(g.x - c2.y * sq, g.y + c2.x * sq);
-      }
-      v[k2] = g;
-    }
+    for (int k2 = 0; k2 < R2; ++k2) v[k2] = slab[(R2 * k1 + k2) * LS + lc];
     dft<R2, +1>(v);
 #pragma unroll
     for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(v[n2], twid[n2 * R1 + k1]);
-    if (dc_col) {
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) dcbuf[R2 * k1 + n2] = v[n2];
-    } else {
-#pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) slab[(R2 * k1 + n2) * LS + lc] = v[n2];
-    }
+    for (int n2 = 0; n2 < R2; ++n2) slab[(R2 * k1 + n2) * LS + lc] = v[n2];
   }
   __syncthreads();
   // inverse pass A' -> H[y = n2 + R2 n1][kx]
@@ -445,10 +473,9 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
     const int task = tid + i * T;
     if (TAh % T != 0 && task >= TAh) break;
     const int n2 = task / CB, lc = task % CB;
-    const bool dc_col = (cb == 0 && lc == 0);
     float2 v[R1];
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) v[k1] = dc_col ? dcbuf[n2 + R2 * k1] : slab[(n2 + R2 * k1) * LS + lc];
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = slab[(n2 + R2 * k1) * LS + lc];
     dft<R1, +1>(v);
     const int kx = CB * cb + lc;  // 0 for the packed (DC, Nyquist) column
 #pragma unroll
@@ -663,7 +690,7 @@ constexpr size_t rows_smem() {
 template <int N>
 constexpr size_t cols_smem() {
   using G = StreamGeom<N>;
-  return sizeof(float2) * (N * (2 * G::CB + 8) + 2 * N);
+  return sizeof(float2) * (N * (2 * G::CB + 8) + N);
 }
 template <int N>
 constexpr size_t irows_smem() {
