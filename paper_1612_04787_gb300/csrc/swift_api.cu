@@ -76,7 +76,10 @@ struct swift_plan_s {
 
 namespace {
 // windows per slice of the streaming path (bounds its workspace)
-constexpr long long kStreamSlice = 2048;
+#ifndef SWIFT_STREAM_SLICE
+#define SWIFT_STREAM_SLICE 2048
+#endif
+constexpr long long kStreamSlice = SWIFT_STREAM_SLICE;
 // windows per slice of the affine / backward path
 constexpr long long kBackSlice = 1024;
 // default forward schedule: 256 x 256 and 128 x 128 windows stream their
