@@ -118,3 +118,83 @@ def test_planted_mistake_is_caught(monkeypatch, name, bad, checks):
         args = () if arg is None else (arg if isinstance(arg, tuple) and fn.__code__.co_argcount == len(arg) else (arg,))
         caught |= _fails(fn, *args)
     assert caught, f"planted mistake in {name} not caught"
+
+
+# --------------------------------------------------------------------------- #
+# the rendering step (mir)
+# --------------------------------------------------------------------------- #
+from oracle import mir  # noqa: E402
+import test_oracle_mir as mir_pins  # noqa: E402
+
+
+def _fit_unweighted_means(q, p, w):
+    q = np.asarray(q, dtype=np.float64).reshape(-1, 2)
+    p = np.asarray(p, dtype=np.float64).reshape(-1, 2)
+    w = np.asarray(w, dtype=np.float64).reshape(-1)
+    if not w.sum() > 0:
+        return mir.identity(), mir.DEGENERATE
+    qb, pb = q.mean(0), p.mean(0)  # plain means instead of weighted ones
+    dq, dp = q - qb, p - pb
+    Sqq = (w[:, None, None] * dq[:, :, None] * dq[:, None, :]).sum(0)
+    Cpq = (w[:, None, None] * dp[:, :, None] * dq[:, None, :]).sum(0)
+    det = np.linalg.det(Sqq)
+    if not det > mir.DET_EPS * (0.5 * np.trace(Sqq)) ** 2:
+        return mir.identity(), mir.DEGENERATE
+    A = Cpq @ np.linalg.inv(Sqq)
+    t = pb - A @ qb
+    return np.array([A[0, 0], A[0, 1], t[0], A[1, 0], A[1, 1], t[1]]), mir.OK
+
+
+def _fit_transposed(q, p, w):
+    th, st = _REAL_FIT(q, p, w)
+    return th[[0, 3, 2, 1, 4, 5]], st  # A^T instead of A
+
+
+_REAL_FIT = mir.fit_affine
+
+
+class _MeshFlippedDiagonal(mir.Mesh):
+    def locate(self, y, x):
+        t = super().locate(y, x)
+        return t ^ 1
+
+
+class _MeshEuclideanBand(mir.Mesh):
+    def supports(self, t, q, band):
+        q = np.asarray(q, dtype=np.float64)
+        _, _, half, y0, x0 = self.triangle(t)
+        c = self.cell
+        dy, dx = q[:, 0] - y0, q[:, 1] - x0
+        box = (dy >= -band) & (dy <= c + band) & (dx >= -band) & (dx <= c + band)
+        diag = (dx - dy >= -band) if half == 0 else (dy - dx >= -band)  # grows the diagonal by b, not 2b
+        return box & diag
+
+
+def _bilinear_swapped(src, Y, X, fill):
+    h, w = src.shape
+    inside = (Y >= 0) & (X >= 0) & (Y <= h - 1) & (X <= w - 1)
+    Yc, Xc = np.where(inside, Y, 0.0), np.where(inside, X, 0.0)
+    y0 = np.minimum(np.floor(Yc).astype(np.int64), h - 2)
+    x0 = np.minimum(np.floor(Xc).astype(np.int64), w - 2)
+    fx, fy = Yc - y0, Xc - x0  # fractions swapped between the axes
+    S = src.astype(np.float64)
+    v = ((1 - fy) * (1 - fx) * S[y0, x0] + (1 - fy) * fx * S[y0, x0 + 1]
+         + fy * (1 - fx) * S[y0 + 1, x0] + fy * fx * S[y0 + 1, x0 + 1])
+    return np.where(inside, v, fill)
+
+
+MIR_MUTATIONS = [
+    ("fit_affine", _fit_unweighted_means, [mir_pins.test_fit_matches_weighted_lstsq]),
+    ("fit_affine", _fit_transposed, [mir_pins.test_fit_recovers_a_known_affine_exactly]),
+    ("Mesh", _MeshFlippedDiagonal, [mir_pins.test_locate_puts_every_pixel_in_its_triangle]),
+    ("Mesh", _MeshEuclideanBand, [mir_pins.test_supports_equal_brute_force_chebyshev_distance]),
+    ("bilinear_fill", _bilinear_swapped, [mir_pins.test_render_identity_translation_and_linear_images]),
+]
+
+
+@pytest.mark.parametrize("name,bad,checks", MIR_MUTATIONS, ids=[f"{m[0]}:{m[1].__name__}" for m in MIR_MUTATIONS])
+def test_planted_mir_mistake_is_caught(monkeypatch, name, bad, checks):
+    for fn in checks:
+        fn()
+    monkeypatch.setattr(mir, name, bad)
+    assert any(_fails(fn) for fn in checks), f"planted mistake in mir.{name} not caught"
