@@ -270,6 +270,75 @@ swift_status swift_plan_replay(swift_plan plan, void* stream);
 swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
 swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, int32_t* launches);
 
+/* ------------------------------------------------------------------------
+ * Rendering step ("mir": Sec. III module list, Sec. IV).  The paper renders
+ * aligned sections from the linear least-squares solution of the swim
+ * correspondence points, as texture mapping of a triangulated mesh whose
+ * triangles are each locally affine, each fitted to the points in and around
+ * it.
+ *
+ * A correspondence is q (output / reference frame), p (source section, the
+ * matching point) and a weight w >= 0, all (y, x): q and p are float32 [P][2],
+ * w float32 [P], device pointers.  An affine maps output to source,
+ * p = A q + t, stored as double[6] = (a_yy, a_yx, t_y, a_xy, a_xx, t_x).
+ * Fits minimise sum_i w_i |A q_i + t - p_i|^2 in FP64.
+ * ------------------------------------------------------------------------ */
+
+/* Triangle mesh: ny x nx square cells of side `cell` (>= 8) from the integer
+ * output-frame corner (origin_y, origin_x); each cell is split by its main
+ * diagonal into triangle 2 (cy nx + cx) + 0, holding the pixels with
+ * (x - x0) >= (y - y0), and + 1, holding the others. */
+typedef struct {
+  int32_t origin_y, origin_x;
+  int32_t cell;
+  int32_t ny, nx;
+} swift_mesh;
+
+/* Fit status (per group / triangle). */
+enum {
+  SWIFT_FIT_OK = 0,
+  SWIFT_FIT_FALLBACK = 1,  /* triangle support degenerate: the all-points affine was used */
+  SWIFT_FIT_DEGENERATE = 2 /* fewer than three non-collinear weighted points: identity   */
+};
+
+/* Correspondences from forward-match results (the swim step's output): for
+ * window b, q = ref_origin[b] + n/2 (the reference window centre),
+ * p = mov_origin[b] + n/2 + (sy, sx) (where that content sits in the moving
+ * section) and w = snr when status is SWIFT_WIN_OK and snr is finite and
+ * >= min_snr, else w = 0 (and p = the moving centre): the SNR-weighted least
+ * squares.  All device pointers: results [B], origins int32 [B][2], q and p
+ * float32 [B][2], w float32 [B]. */
+swift_status swift_correspondences(const swift_result* results, const int32_t* ref_origin,
+                                   const int32_t* mov_origin, int64_t n_windows, int32_t n, float min_snr, float* q,
+                                   float* p, float* w, void* stream);
+
+/* One weighted least-squares affine per group: group g owns points
+ * [offsets[g], offsets[g+1]) (offsets: device int64 [n_groups + 1]).
+ * theta: device double [n_groups][6]; status: device int32 [n_groups].  A
+ * group is degenerate (identity written) when its weights sum to 0 or its
+ * weighted points are (nearly) collinear: det(Sqq) <= 1e-9 (tr Sqq / 2)^2 for
+ * the weighted centred second moments Sqq.  Stream-ordered. */
+swift_status swift_fit_affine(const float* q, const float* p, const float* w, const int64_t* offsets,
+                              int32_t n_groups, double* theta, int32_t* status, void* stream);
+
+/* One affine per mesh triangle (theta: device double [2 ny nx][6], status:
+ * device int32 [2 ny nx]), each fitted to the points within Chebyshev
+ * distance `band` (>= 0, output pixels) of the closed triangle: the
+ * triangle's own area plus a surrounding band (band = cell takes in the
+ * neighbouring triangles).  Degenerate supports take the all-points affine
+ * (SWIFT_FIT_FALLBACK), or the identity when that is degenerate too. */
+swift_status swift_mesh_fit(const float* q, const float* p, const float* w, int64_t n_points,
+                            const swift_mesh* mesh, int32_t band, double* theta, int32_t* status, void* stream);
+
+/* Texture-map one source section (src: a uint8 / float32 image, height and
+ * width >= 2, pitch in elements) through the mesh into out (device float32
+ * [out_h][out_pitch]): output pixel (y, x) belongs to the triangle of its
+ * cell (cells clamped to the mesh) and takes the bilinear sample of the
+ * source at A (y, x) + t, or `fill` where that point leaves
+ * [0, h-1] x [0, w-1].  theta as written by swift_mesh_fit. */
+swift_status swift_render(const swift_image* src, swift_dtype dtype, const double* theta, const swift_mesh* mesh,
+                          float* out, int32_t out_h, int32_t out_w, int64_t out_pitch, float fill, void* stream);
+
 /* Set the whitening exponent of one level for later calls (w in [0, 1]). */
 swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w);
 

@@ -176,3 +176,21 @@ def render(src: np.ndarray, thetas, mesh: Mesh, out_h: int, out_w: int, fill: fl
     py = th[..., 0] * Y + th[..., 1] * X + th[..., 2]
     px = th[..., 3] * Y + th[..., 4] * X + th[..., 5]
     return bilinear_fill(src, py, px, fill)
+
+
+def correspondences(results, ref_origins, mov_origins, n: int, min_snr: float = 0.0):
+    """(q, p, w) from swim results (list of dicts): q = reference window
+    centre, p = moving window centre + subpixel shift (where the reference
+    content sits in the moving section), w = SNR of OK windows with a finite
+    SNR >= min_snr, else 0 (p then the moving centre)."""
+    B = len(results)
+    q = np.zeros((B, 2))
+    p = np.zeros((B, 2))
+    w = np.zeros(B)
+    c = n / 2.0
+    for b, r in enumerate(results):
+        q[b] = (ref_origins[b][0] + c, ref_origins[b][1] + c)
+        ok = r["status"] == 0 and np.isfinite(r["snr"]) and r["snr"] >= min_snr
+        p[b] = (mov_origins[b][0] + c + (r["sy"] if ok else 0.0), mov_origins[b][1] + c + (r["sx"] if ok else 0.0))
+        w[b] = r["snr"] if ok else 0.0
+    return q, p, w

@@ -19,11 +19,13 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (APOD, DTYPE, PRECISION, SwiftBatch, SwiftImage, SwiftLevel, SwiftError,  # noqa: F401
-                   WIN_FLAT, WIN_NONFINITE, WIN_OK, WIN_OUT_OF_BOUNDS, check, lib)
+from ._lib import (APOD, DTYPE, PRECISION, SwiftBatch, SwiftImage, SwiftLevel, SwiftMesh, SwiftError,  # noqa: F401
+                   FIT_DEGENERATE, FIT_FALLBACK, FIT_OK, WIN_FLAT, WIN_NONFINITE, WIN_OK, WIN_OUT_OF_BOUNDS, check,
+                   lib)
 
 __all__ = ["Level", "Plan", "decode", "SwiftError", "version", "match_warped", "WIN_OK", "WIN_OUT_OF_BOUNDS",
-           "WIN_FLAT", "WIN_NONFINITE"]
+           "WIN_FLAT", "WIN_NONFINITE", "Mesh", "correspondences", "fit_affine", "mesh_fit", "render",
+           "FIT_OK", "FIT_FALLBACK", "FIT_DEGENERATE"]
 
 
 def version() -> str:
@@ -268,3 +270,98 @@ def decode(res) -> dict:
     f = a.view(np.float32)
     return {"dy": a[:, 0].copy(), "dx": a[:, 1].copy(), "sy": f[:, 2].copy(), "sx": f[:, 3].copy(),
             "snr": f[:, 4].copy(), "peak": f[:, 5].copy(), "status": a[:, 6].copy()}
+
+
+# --------------------------------------------------------------------------- #
+# rendering step (mir): least-squares affines, triangle mesh, texture mapping
+# --------------------------------------------------------------------------- #
+@dataclass
+class Mesh:
+    """ny x nx square cells of side ``cell`` (>= 8) from the output-frame
+    corner (origin_y, origin_x); two triangles per cell (Sec. IV)."""
+    origin_y: int
+    origin_x: int
+    cell: int
+    ny: int
+    nx: int
+
+    @property
+    def n_triangles(self) -> int:
+        return 2 * self.ny * self.nx
+
+    def c(self) -> SwiftMesh:
+        return SwiftMesh(int(self.origin_y), int(self.origin_x), int(self.cell), int(self.ny), int(self.nx))
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, shape_tail, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} must have shape [N, {', '.join(map(str, shape_tail))}]")
+    return t
+
+
+def correspondences(res, ref_origin, mov_origin, n: int, min_snr: float = 0.0, stream=None):
+    """(q, p, w) from forward-match results: reference window centres, the
+    matching moving-section points, and SNR weights (0 for failed windows)."""
+    B = int(res.shape[0])
+    dev = res.device
+    q = torch.empty((B, 2), dtype=torch.float32, device=dev)
+    p = torch.empty((B, 2), dtype=torch.float32, device=dev)
+    w = torch.empty((B,), dtype=torch.float32, device=dev)
+    check(lib.swift_correspondences(res.data_ptr(), ref_origin.data_ptr(), mov_origin.data_ptr(), B, int(n),
+                                    float(min_snr), q.data_ptr(), p.data_ptr(), w.data_ptr(), _stream_ptr(stream)),
+          "swift_correspondences")
+    return q, p, w
+
+
+def fit_affine(q, p, w, offsets=None, stream=None):
+    """Weighted least-squares affines p ~ A q + t, one per group of points
+    (``offsets`` int64 [G + 1], default one group).  Returns (theta [G, 6]
+    float64, status [G] int32) on the device."""
+    _dev(q, torch.float32, (2,), "q")
+    _dev(p, torch.float32, (2,), "p")
+    if w.shape[0] != q.shape[0] or p.shape[0] != q.shape[0]:
+        raise ValueError("q, p and w must have the same length")
+    if offsets is None:
+        offsets = torch.tensor([0, q.shape[0]], dtype=torch.int64, device=q.device)
+    G = int(offsets.shape[0]) - 1
+    theta = torch.empty((G, 6), dtype=torch.float64, device=q.device)
+    status = torch.empty((G,), dtype=torch.int32, device=q.device)
+    check(lib.swift_fit_affine(q.data_ptr(), p.data_ptr(), w.data_ptr(), offsets.data_ptr(), G, theta.data_ptr(),
+                               status.data_ptr(), _stream_ptr(stream)), "swift_fit_affine")
+    return theta, status
+
+
+def mesh_fit(q, p, w, mesh: Mesh, band: int, stream=None):
+    """Per-triangle affines [2 ny nx, 6] (float64) and statuses, each fitted
+    to the points within Chebyshev distance ``band`` of its triangle."""
+    _dev(q, torch.float32, (2,), "q")
+    _dev(p, torch.float32, (2,), "p")
+    if w.shape[0] != q.shape[0] or p.shape[0] != q.shape[0]:
+        raise ValueError("q, p and w must have the same length")
+    theta = torch.empty((mesh.n_triangles, 6), dtype=torch.float64, device=q.device)
+    status = torch.empty((mesh.n_triangles,), dtype=torch.int32, device=q.device)
+    mc = mesh.c()
+    check(lib.swift_mesh_fit(q.data_ptr(), p.data_ptr(), w.data_ptr(), q.shape[0], C.byref(mc), int(band),
+                             theta.data_ptr(), status.data_ptr(), _stream_ptr(stream)), "swift_mesh_fit")
+    return theta, status
+
+
+def render(src, theta, mesh: Mesh, out_h: int, out_w: int, fill: float = 0.0, out=None, stream=None):
+    """Texture-map ``src`` ([H, W] uint8 / float32 CUDA tensor) through the
+    mesh's triangle affines into a float32 [out_h, out_w] image."""
+    if src.dtype not in (torch.uint8, torch.float32) or src.dim() != 2:
+        raise TypeError("src must be a [H, W] uint8 or float32 CUDA tensor")
+    img = _image(src, src.dtype, False)
+    if theta.dtype != torch.float64 or tuple(theta.shape) != (mesh.n_triangles, 6) or not theta.is_contiguous():
+        raise ValueError("theta must be a contiguous float64 [2 ny nx, 6] tensor")
+    if out is None:
+        out = torch.empty((out_h, out_w), dtype=torch.float32, device=src.device)
+    elif out.dtype != torch.float32 or out.dim() != 2 or out.shape[0] < out_h or out.stride(1) != 1:
+        raise ValueError("out must be a float32 [out_h, >= out_w] tensor with contiguous rows")
+    mc = mesh.c()
+    check(lib.swift_render(C.byref(img), DTYPE["u8" if src.dtype == torch.uint8 else "f32"], theta.data_ptr(),
+                           C.byref(mc), out.data_ptr(), int(out_h), int(out_w), out.stride(0), float(fill),
+                           _stream_ptr(stream)), "swift_render")
+    return out

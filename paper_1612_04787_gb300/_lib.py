@@ -43,7 +43,13 @@ EXPORTS = (
     "swift_plan_timings",
     "swift_status_string",
     "swift_version",
+    "swift_correspondences",
+    "swift_fit_affine",
+    "swift_mesh_fit",
+    "swift_render",
 )
+
+FIT_OK, FIT_FALLBACK, FIT_DEGENERATE = 0, 1, 2
 
 
 class SwiftLevel(C.Structure):
@@ -69,6 +75,11 @@ class SwiftResult(C.Structure):
 
 
 assert C.sizeof(SwiftResult) == 32
+
+
+class SwiftMesh(C.Structure):
+    _fields_ = [("origin_y", C.c_int32), ("origin_x", C.c_int32), ("cell", C.c_int32),
+                ("ny", C.c_int32), ("nx", C.c_int32)]
 
 
 def _load():
@@ -108,6 +119,18 @@ def _load():
     lib.swift_status_string.restype = C.c_char_p
     lib.swift_version.argtypes = []
     lib.swift_version.restype = C.c_char_p
+    lib.swift_correspondences.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_float,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.swift_correspondences.restype = C.c_int
+    lib.swift_fit_affine.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
+    lib.swift_fit_affine.restype = C.c_int
+    lib.swift_mesh_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(SwiftMesh), C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.swift_mesh_fit.restype = C.c_int
+    lib.swift_render.argtypes = [C.POINTER(SwiftImage), C.c_int, C.c_void_p, C.POINTER(SwiftMesh), C.c_void_p,
+                                 C.c_int32, C.c_int32, C.c_int64, C.c_float, C.c_void_p]
+    lib.swift_render.restype = C.c_int
     return lib
 
 

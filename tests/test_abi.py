@@ -66,3 +66,23 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).replace("the oracle", ""), f
+
+
+def test_mir_argument_errors_before_any_launch():
+    """Invalid meshes, sizes and pointers are rejected on the host."""
+    import ctypes as C
+    from paper_1612_04787_gb300 import _lib
+    lib = _lib.lib
+    bad = _lib.SwiftMesh(0, 0, 4, 2, 2)  # cell below 8
+    good = _lib.SwiftMesh(0, 0, 16, 2, 2)
+    dummy = C.c_void_p(16)
+    assert lib.swift_mesh_fit(dummy, dummy, dummy, 1, C.byref(bad), 0, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_mesh_fit(dummy, dummy, dummy, 1, C.byref(good), -1, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_mesh_fit(None, None, None, 1, C.byref(good), 0, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
+    img = _lib.SwiftImage(None, 8, 0, 8, 8, 1)
+    assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 8, 8, 8, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
+    img = _lib.SwiftImage(16, 8, 0, 8, 8, 1)
+    assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 8, 8, 4, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_fit_affine(dummy, dummy, dummy, dummy, -1, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_fit_affine(None, None, None, None, 0, None, None, None) == _lib.SWIFT_OK
+    assert lib.swift_correspondences(None, None, None, 4, 64, 0.0, None, None, None, None) == _lib.SWIFT_ERR_INVALID_ARG

@@ -128,3 +128,21 @@ def test_render_identity_translation_and_linear_images():
     ok = ~np.isnan(out.ravel())
     assert ok.mean() > 0.5
     np.testing.assert_allclose(out.ravel()[ok], want[ok], rtol=1e-12, atol=1e-9)
+
+
+def test_correspondences_follow_a_physical_translation():
+    """Content shifted by (+3, -5) in the moving section: swim's shift and the
+    correspondence point p = q + shift must point to where it went."""
+    import synth
+    from oracle import swim
+    a, _ = synth.em_section_pair(512, seed_content=31, seed_warp=32, seed_noise=(33, 34))
+    b = np.roll(a, (3, -5), axis=(0, 1))
+    lv = swim.Level(64, 0.65, swim.APOD_HANN, 1.0, 3.0)
+    org = [(100, 120), (300, 260), (220, 380)]
+    res = [swim.match_pair(swim.gather(b, o, 64), swim.gather(a, o, 64), lv) for o in org]
+    q, p, w = mir.correspondences(res, org, org, 64)
+    np.testing.assert_allclose(p - q, np.broadcast_to([3.0, -5.0], (3, 2)), atol=0.05)
+    np.testing.assert_allclose(q, np.array(org) + 32.0)
+    assert (w > 5).all()
+    bad = dict(res[0], status=1)
+    assert mir.correspondences([bad], org[:1], org[:1], 64)[2][0] == 0.0
