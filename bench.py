@@ -15,6 +15,9 @@ Other workloads (``--workload``):
   warp        2048 windows of 128 x 128 on a 9-section stack: reference = mean of the
               8 neighbours, moving = resampled under per-window affine warps; a step is
               the forward and the backward of loss = -sum snr * peak
+  mir         the rendering step: per-triangle affine fit to the SNR-weighted swim
+              correspondences of the headline grid and texture mapping of the 4096^2
+              moving section (metric: output pixels/s)
 
 All inputs are seeded synthetic stand-ins for the paper's ssEM sections
 (``synth``).  Timing: W warm-up steps, then K timed steps; L2 is flushed (256 MiB
@@ -600,6 +603,136 @@ def make_workload(name, torch, swift, dev, args):
 
 
 # --------------------------------------------------------------------------- #
+# the rendering step (mir): mesh fit + texture mapping of a whole section
+# --------------------------------------------------------------------------- #
+MIR_METRIC = "rendered output pixels/sec (mir: per-triangle SNR-weighted affine fit + texture mapping)"
+
+
+def mir_main(args, torch, swift, dev, world, rank):
+    """Workload: the headline section pair's swim grid (31 x 31 windows of
+    256^2, computed once) gives SNR-weighted correspondences; a step fits one
+    affine per triangle of a 16 x 16-cell mesh (cell 256 px, band 256 px) and
+    renders the moving section (uint8, 4096^2) into the reference frame as
+    float32.  Metric: output pixels per second."""
+    import synth
+    size, n, stride, cell = 4096, 256, 128, 256
+    a, b = synth.em_section_pair(size)
+    org = synth.grid_origins(size, n, stride)
+    da, db = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    dorg = torch.from_numpy(org).to(dev)
+    plan = swift.Plan([swift.Level(n, 0.65, "hann", 1.0, 3.0)], dtype="u8", max_windows=len(org))
+    res = plan.match(da, db, dorg, dorg)
+    q, p, w = swift.correspondences(res, dorg, dorg, n, min_snr=5.0)
+    mesh = swift.Mesh(0, 0, cell, size // cell, size // cell)
+    band = cell
+    out = torch.empty((size, size), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    recs = torch.empty((mesh.n_triangles, 8), dtype=torch.float32, device=dev)
+
+    def step():
+        th, st = swift.mesh_fit(q, p, w, mesh, band, stream=stream)
+        swift.render_records(th, mesh, records=recs, stream=stream)
+        swift.render(db, th, mesh, size, size, fill=0.0, out=out, records=recs, stream=stream)
+        return th, st
+
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        th, st = step()
+    torch.cuda.synchronize(dev)
+    ok_frac = float((st == swift.FIT_OK).float().mean())
+    sampler = ClockSampler(local_rank())
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        th, _ = swift.mesh_fit(q, p, w, mesh, band, stream=stream)
+        swift.render_records(th, mesh, records=recs, stream=stream)
+        mids[k].record(stream)
+        swift.render(db, th, mesh, size, size, fill=0.0, out=out, records=recs, stream=stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    fit_ms = sum(s_.elapsed_time(m_) for s_, m_ in zip(starts, mids)) / args.steps
+    render_ms = sum(m_.elapsed_time(e_) for m_, e_ in zip(mids, ends)) / args.steps
+    px = size * size
+    total_ms, value = aggregate_over_ranks(total_ms, px, args.steps, world, dev)
+    print(f"[bench] mir rank {rank}: {args.steps} steps, {total_ms / args.steps:.4f} ms/step "
+          f"(fit {fit_ms:.4f}, render {render_ms:.4f}), {value / 1e9:.3f} Gpx/s", file=sys.stderr, flush=True)
+
+    # e2e: section and correspondences in from pinned host memory, image out
+    hb = b.copy()
+    hb_t = torch.from_numpy(hb).pin_memory()
+    hq, hp, hw = q.cpu().pin_memory(), p.cpu().pin_memory(), w.cpu().pin_memory()
+    hout = torch.empty((size, size), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        db.copy_(hb_t, non_blocking=True)
+        q.copy_(hq, non_blocking=True)
+        p.copy_(hp, non_blocking=True)
+        w.copy_(hw, non_blocking=True)
+        step()
+        hout.copy_(out, non_blocking=True)
+        stream.synchronize()
+    e2e_value = world * px * e2e_steps / (time.perf_counter() - t0)
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    algo_bytes = px * (1 + 4)  # uint8 source read once, float32 written
+    achieved = algo_bytes / (render_ms / 1e3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import mir as omir
+        qn, pn, wn = q.cpu().numpy(), p.cpu().numpy(), w.cpu().numpy()
+        rows = np.arange(0, size, 16)  # every 16th output row
+        t0 = time.perf_counter()
+        oth, _ = omir.mesh_fit(qn, pn, wn, omir.Mesh(0, 0, cell, size // cell, size // cell), band)
+        omir.render(b, oth, omir.Mesh(0, 0, cell, size // cell, size // cell), size, size, 0.0, rows=rows)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(rows) * size / dt, "unit": "pixels/s", "cores": 1, "kind": "oracle",
+               "sample": f"mesh fit of all {mesh.n_triangles} triangles + {len(rows)} of {size} output rows "
+                         f"(every 16th), FP64 numpy, one process ({dt:.1f} s)"}
+    line = {
+        "metric": MIR_METRIC, "value": value, "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
+        "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64 fits)", "data": "synthetic",
+        "config": {"workload": f"mir: {mesh.n_triangles}-triangle mesh (cell {cell}, band {band}) fitted to the "
+                               f"SNR-weighted swim correspondences of the {len(org)}-window 256^2 grid, "
+                               f"{size}x{size} uint8 moving section rendered as float32",
+                   "name": "mir", "fit_ok_fraction": ok_frac, "fit_ms": fit_ms, "render_ms": render_ms,
+                   "l2": "flushed before every timed step (256 MiB write, outside the step's events)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "render_kernel<u8>",
+                     "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); algorithmic bytes = 1 B "
+                                  "source + 4 B output per pixel"},
+        "e2e": {"value": e2e_value, "unit": "pixels/s", "h2d_bytes_per_step": int(hb.nbytes + 5 * 4 * len(org)),
+                "d2h_bytes_per_step": int(px * 4)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def local_rank() -> int:
+    return int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# --------------------------------------------------------------------------- #
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -663,7 +796,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sections",
-                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp"])
+                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "mir"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2", "fp16x2"])
     ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (sections workload)")
     ap.add_argument("--windows", type=int, default=0, help="limit the windows per step (small profiling cases)")
@@ -687,6 +820,11 @@ def main():
     torch.cuda.set_device(dev)
     import paper_1612_04787_gb300 as swift
 
+    if args.workload == "mir":
+        mir_main(args, torch, swift, dev, world, rank)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     W = make_workload(args.workload, torch, swift, dev, args)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -24,7 +24,7 @@ from ._lib import (APOD, DTYPE, PRECISION, SwiftBatch, SwiftImage, SwiftLevel, S
                    lib)
 
 __all__ = ["Level", "Plan", "decode", "SwiftError", "version", "match_warped", "WIN_OK", "WIN_OUT_OF_BOUNDS",
-           "WIN_FLAT", "WIN_NONFINITE", "Mesh", "correspondences", "fit_affine", "mesh_fit", "render",
+           "WIN_FLAT", "WIN_NONFINITE", "Mesh", "correspondences", "fit_affine", "mesh_fit", "render", "render_records",
            "FIT_OK", "FIT_FALLBACK", "FIT_DEGENERATE"]
 
 
@@ -348,20 +348,34 @@ def mesh_fit(q, p, w, mesh: Mesh, band: int, stream=None):
     return theta, status
 
 
-def render(src, theta, mesh: Mesh, out_h: int, out_w: int, fill: float = 0.0, out=None, stream=None):
+def render_records(theta, mesh: Mesh, records=None, stream=None):
+    """Per-triangle render records (FP64 work done once per mesh)."""
+    if theta.dtype != torch.float64 or tuple(theta.shape) != (mesh.n_triangles, 6) or not theta.is_contiguous():
+        raise ValueError("theta must be a contiguous float64 [2 ny nx, 6] tensor")
+    if records is None:
+        records = torch.empty((mesh.n_triangles, 8), dtype=torch.float32, device=theta.device)
+    mc = mesh.c()
+    check(lib.swift_render_prepare(theta.data_ptr(), C.byref(mc), records.data_ptr(), _stream_ptr(stream)),
+          "swift_render_prepare")
+    return records
+
+
+def render(src, theta, mesh: Mesh, out_h: int, out_w: int, fill: float = 0.0, out=None, records=None,
+           stream=None):
     """Texture-map ``src`` ([H, W] uint8 / float32 CUDA tensor) through the
-    mesh's triangle affines into a float32 [out_h, out_w] image."""
+    mesh's triangle affines into a float32 [out_h, out_w] image.  ``records``
+    (from ``render_records``) skips the per-mesh preparation."""
     if src.dtype not in (torch.uint8, torch.float32) or src.dim() != 2:
         raise TypeError("src must be a [H, W] uint8 or float32 CUDA tensor")
     img = _image(src, src.dtype, False)
-    if theta.dtype != torch.float64 or tuple(theta.shape) != (mesh.n_triangles, 6) or not theta.is_contiguous():
-        raise ValueError("theta must be a contiguous float64 [2 ny nx, 6] tensor")
+    if records is None:
+        records = render_records(theta, mesh, stream=stream)
     if out is None:
         out = torch.empty((out_h, out_w), dtype=torch.float32, device=src.device)
     elif out.dtype != torch.float32 or out.dim() != 2 or out.shape[0] < out_h or out.stride(1) != 1:
         raise ValueError("out must be a float32 [out_h, >= out_w] tensor with contiguous rows")
     mc = mesh.c()
-    check(lib.swift_render(C.byref(img), DTYPE["u8" if src.dtype == torch.uint8 else "f32"], theta.data_ptr(),
+    check(lib.swift_render(C.byref(img), DTYPE["u8" if src.dtype == torch.uint8 else "f32"], records.data_ptr(),
                            C.byref(mc), out.data_ptr(), int(out_h), int(out_w), out.stride(0), float(fill),
                            _stream_ptr(stream)), "swift_render")
     return out

@@ -46,6 +46,7 @@ EXPORTS = (
     "swift_correspondences",
     "swift_fit_affine",
     "swift_mesh_fit",
+    "swift_render_prepare",
     "swift_render",
 )
 
@@ -128,6 +129,8 @@ def _load():
     lib.swift_mesh_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(SwiftMesh), C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p]
     lib.swift_mesh_fit.restype = C.c_int
+    lib.swift_render_prepare.argtypes = [C.c_void_p, C.POINTER(SwiftMesh), C.c_void_p, C.c_void_p]
+    lib.swift_render_prepare.restype = C.c_int
     lib.swift_render.argtypes = [C.POINTER(SwiftImage), C.c_int, C.c_void_p, C.POINTER(SwiftMesh), C.c_void_p,
                                  C.c_int32, C.c_int32, C.c_int64, C.c_float, C.c_void_p]
     lib.swift_render.restype = C.c_int

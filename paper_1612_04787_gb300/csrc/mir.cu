@@ -20,10 +20,11 @@
 // support is degenerate take the whole-point-set affine (FALLBACK), else the
 // identity (DEGENERATE).
 //
-// Render: 32 x 32 output tiles, one CTA each.  The CTA turns the (at most 50)
-// triangles under its tile into records in FP64: for the triangle's cell
-// origin q0, p0 = A q0 + t split into an integer base and an FP32 fraction.
-// Each pixel then needs only small-magnitude FP32 arithmetic,
+// Render: a prepare kernel turns each triangle's affine into a record in FP64
+// (once per mesh: the FP64 unit of this GPU is slow): for the triangle's cell
+// corner q0, p0 = A q0 + t split into an integer base and an FP32 fraction.
+// The render kernel (32 x 32 output tiles, 256 threads) reads records through
+// L1, and each pixel needs only small-magnitude FP32 arithmetic,
 // p = base + (frac + A (q - q0)), so large section coordinates cost no
 // accuracy.  Bilinear sampling as the oracle: samples outside
 // [0, h-1] x [0, w-1] take the fill value; the last row / column interpolate
@@ -40,10 +41,10 @@ namespace swift {
 namespace {
 
 constexpr int kFitThreads = 256;
+constexpr int kMeshFitThreads = 64;
 constexpr double kDetEps = 1e-9;
 constexpr int kTile = 32;
 constexpr int kMinCell = 8;
-constexpr int kMaxRecCells = kTile / kMinCell + 1;  // cells per tile side
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -73,6 +74,7 @@ struct Moments {
 };
 
 // block-wide sum of the moments (deterministic tree); result valid in thread 0
+template <int NT>
 __device__ void block_sum(Moments& m, double (*sh)[12]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* a = m.as_array();
@@ -85,7 +87,7 @@ __device__ void block_sum(Moments& m, double (*sh)[12]) {
   if (threadIdx.x == 0) {
     for (int k = 0; k < 12; ++k) {
       double s = 0.0;
-      for (int v = 0; v < kFitThreads / 32; ++v) s += sh[v][k];
+      for (int v = 0; v < NT / 32; ++v) s += sh[v][k];
       a[k] = s;
     }
   }
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kFitThreads) fit_groups_kernel(const float* q,
     const double wi = w[i];
     if (wi > 0.0) m.add(wi, q[2 * i] - cy, q[2 * i + 1] - cx, p[2 * i] - cy, p[2 * i + 1] - cx);
   }
-  block_sum(m, sh);
+  block_sum<kFitThreads>(m, sh);
   if (threadIdx.x == 0) {
     double th[6];
     int st = solve_affine(m, cy, cx, th);
@@ -143,10 +145,10 @@ __global__ void __launch_bounds__(kFitThreads) fit_groups_kernel(const float* q,
   }
 }
 
-__global__ void __launch_bounds__(kFitThreads) mesh_fit_kernel(const float* q, const float* p, const float* w,
-                                                               int64_t n, swift_mesh mesh, int32_t band,
-                                                               double* theta, int32_t* status) {
-  __shared__ double sh[kFitThreads / 32][12];
+__global__ void __launch_bounds__(kMeshFitThreads) mesh_fit_kernel(const float* q, const float* p, const float* w,
+                                                                   int64_t n, swift_mesh mesh, int32_t band,
+                                                                   double* theta, int32_t* status) {
+  __shared__ double sh[kMeshFitThreads / 32][12];
   __shared__ int st_sh;
   const int t = blockIdx.x;
   const int c = t >> 1, half = t & 1;
@@ -156,28 +158,36 @@ __global__ void __launch_bounds__(kFitThreads) mesh_fit_kernel(const float* q, c
   const double lo = -static_cast<double>(band), hi = static_cast<double>(mesh.cell) + band, dg = -2.0 * band;
   Moments m;
   m.zero();
-  for (int64_t i = threadIdx.x; i < n; i += kFitThreads) {
-    const double wi = w[i];
-    if (!(wi > 0.0)) continue;
-    const double dy = static_cast<double>(q[2 * i]) - y0, dx = static_cast<double>(q[2 * i + 1]) - x0;
+  // FP32 prefilter with a 1 px margin (never rejects a supporting point), then
+  // the exact FP64 test on the few candidates
+  const float y0f = static_cast<float>(y0), x0f = static_cast<float>(x0);
+  const float lof = static_cast<float>(lo) - 1.f, hif = static_cast<float>(hi) + 1.f;
+  for (int64_t i = threadIdx.x; i < n; i += kMeshFitThreads) {
+    const float wf = w[i];
+    if (!(wf > 0.f)) continue;
+    const float qyf = q[2 * i], qxf = q[2 * i + 1];
+    const float ey = qyf - y0f, ex = qxf - x0f;
+    if (!(ey >= lof && ey <= hif && ex >= lof && ex <= hif)) continue;
+    const double wi = wf;
+    const double dy = static_cast<double>(qyf) - y0, dx = static_cast<double>(qxf) - x0;
     const bool box = dy >= lo && dy <= hi && dx >= lo && dx <= hi;
     const bool diag = half == 0 ? (dx - dy >= dg) : (dy - dx >= dg);
     if (box && diag) m.add(wi, dy, dx, static_cast<double>(p[2 * i]) - y0, static_cast<double>(p[2 * i + 1]) - x0);
   }
-  block_sum(m, sh);
+  block_sum<kMeshFitThreads>(m, sh);
   double th[6];
   if (threadIdx.x == 0) st_sh = solve_affine(m, y0, x0, th);
   __syncthreads();
   if (st_sh != SWIFT_FIT_OK) {  // whole-point-set affine, centred on the mesh centre
     const double gy = mesh.origin_y + 0.5 * mesh.cell * mesh.ny, gx = mesh.origin_x + 0.5 * mesh.cell * mesh.nx;
     m.zero();
-    for (int64_t i = threadIdx.x; i < n; i += kFitThreads) {
+    for (int64_t i = threadIdx.x; i < n; i += kMeshFitThreads) {
       const double wi = w[i];
       if (wi > 0.0)
         m.add(wi, static_cast<double>(q[2 * i]) - gy, static_cast<double>(q[2 * i + 1]) - gx,
               static_cast<double>(p[2 * i]) - gy, static_cast<double>(p[2 * i + 1]) - gx);
     }
-    block_sum(m, sh);
+    block_sum<kMeshFitThreads>(m, sh);
     if (threadIdx.x == 0) {
       st_sh = solve_affine(m, gy, gx, th) == SWIFT_FIT_OK ? SWIFT_FIT_FALLBACK : SWIFT_FIT_DEGENERATE;
       if (st_sh == SWIFT_FIT_DEGENERATE) write_identity(th);
@@ -189,95 +199,173 @@ __global__ void __launch_bounds__(kFitThreads) mesh_fit_kernel(const float* q, c
   }
 }
 
-struct RenderRec {
+// per-triangle render record (32 bytes): A in FP32, and p0 = A q0 + t for the
+// triangle's cell corner q0 split into an FP32 fraction and an integer base
+struct __align__(16) RenderRec {
   float a_yy, a_yx, a_xy, a_xx;  // A
-  float fy, fx;                  // fraction of p0 = A q0 + t
+  float fy, fx;                  // fraction of p0
   int by, bx;                    // integer part of p0
 };
+static_assert(sizeof(RenderRec) == 32, "record layout");
 
-template <typename TIn>
-__device__ __forceinline__ float src_px(const TIn* s, long long pitch, int y, int x) {
-  return static_cast<float>(s[static_cast<long long>(y) * pitch + x]);
+// Per-pixel arithmetic avoids conversion instructions (int <-> float, floor,
+// integer division), which share the slow double-precision / conversion unit
+// on this GPU: small integers become floats through the exponent trick, and
+// floor comes from the 1.5 * 2^23 rounding trick.
+__device__ __forceinline__ float u8_to_float(uint32_t v) {  // v < 2^23
+  return __int_as_float(0x4B000000 | static_cast<int>(v)) - 8388608.0f;
+}
+// |v| < 2^22 (pixel offsets from their cell, bounded by the render size limits)
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+__device__ __forceinline__ float src_val(const uint8_t* s) { return u8_to_float(__ldg(s)); }
+__device__ __forceinline__ float src_val(const float* s) { return __ldg(s); }
+// floor of v (|v| < 2^22) as an integer and the fraction v - floor(v) in [0, 1)
+__device__ __forceinline__ int floor_frac(float v, float& frac) {
+  const float r = v + 12582912.0f;  // 1.5 * 2^23: r's low mantissa bits hold round(v)
+  int ri = __float_as_int(r) - 0x4B400000;
+  float rf = r - 12582912.0f;       // round(v), exactly
+  if (rf > v) {
+    ri -= 1;
+    rf -= 1.0f;
+  }
+  frac = v - rf;
+  return ri;
 }
 
-template <typename TIn>
-__global__ void __launch_bounds__(256) render_kernel(const TIn* src, long long src_pitch, int src_h, int src_w,
-                                                     const double* theta, swift_mesh mesh, float* out,
-                                                     long long out_pitch, int out_h, int out_w, float fill) {
-  __shared__ RenderRec rec[kMaxRecCells * kMaxRecCells * 2];
+// one thread per triangle: the FP64 part of rendering, done once per mesh
+__global__ void render_prepare_kernel(const double* theta, swift_mesh mesh, RenderRec* rec, int n_tri) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tri) return;
+  const int c = t >> 1;
+  const int cy = c / mesh.nx, cx = c % mesh.nx;
+  const double* th = theta + 6 * t;
+  const double q0y = static_cast<double>(mesh.origin_y) + static_cast<double>(cy) * mesh.cell;
+  const double q0x = static_cast<double>(mesh.origin_x) + static_cast<double>(cx) * mesh.cell;
+  const double p0y = th[0] * q0y + th[1] * q0x + th[2];
+  const double p0x = th[3] * q0y + th[4] * q0x + th[5];
+  const double by = floor(p0y), bx = floor(p0x);
+  RenderRec R;
+  R.a_yy = static_cast<float>(th[0]);
+  R.a_yx = static_cast<float>(th[1]);
+  R.a_xy = static_cast<float>(th[3]);
+  R.a_xx = static_cast<float>(th[4]);
+  R.fy = static_cast<float>(p0y - by);
+  R.fx = static_cast<float>(p0x - bx);
+  // bases far outside any section saturate (their pixels take the fill value)
+  R.by = static_cast<int>(fmin(fmax(by, -1e9), 1e9));
+  R.bx = static_cast<int>(fmin(fmax(bx, -1e9), 1e9));
+  rec[t] = R;
+}
+
+// IDX: int for images below 2^31 elements (cheaper address arithmetic), else long long
+template <typename TIn, typename IDX>
+__global__ void __launch_bounds__(256) render_kernel(const TIn* src, IDX src_pitch, int src_h, int src_w,
+                                                     const RenderRec* rec, swift_mesh mesh, float* out,
+                                                     IDX out_pitch, int out_h, int out_w, float fill) {
   const int ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
-  // cell of an output coordinate: floor division in integers, clamped to the mesh
-  auto cell_i = [&](int v, int o, int n) {
-    int d = v - o;
-    int c = d >= 0 ? d / mesh.cell : -((-d + mesh.cell - 1) / mesh.cell);
-    return c < 0 ? 0 : (c >= n ? n - 1 : c);
-  };
-  const int cy_lo = cell_i(ty0, mesh.origin_y, mesh.ny), cy_hi = cell_i(ty0 + kTile - 1, mesh.origin_y, mesh.ny);
-  const int cx_lo = cell_i(tx0, mesh.origin_x, mesh.nx), cx_hi = cell_i(tx0 + kTile - 1, mesh.origin_x, mesh.nx);
-  const int ncx = cx_hi - cx_lo + 1;
-  const int nrec = (cy_hi - cy_lo + 1) * ncx * 2;
-  for (int r = threadIdx.x; r < nrec; r += 256) {
-    const int half = r & 1, cl = r >> 1;
-    const int cy = cy_lo + cl / ncx, cx = cx_lo + cl % ncx;
-    const double* th = theta + 6 * (2 * (cy * mesh.nx + cx) + half);
-    const double q0y = static_cast<double>(mesh.origin_y) + static_cast<double>(cy) * mesh.cell;
-    const double q0x = static_cast<double>(mesh.origin_x) + static_cast<double>(cx) * mesh.cell;
-    const double p0y = th[0] * q0y + th[1] * q0x + th[2];
-    const double p0x = th[3] * q0y + th[4] * q0x + th[5];
-    const double by = floor(p0y), bx = floor(p0x);
-    RenderRec R;
-    R.a_yy = static_cast<float>(th[0]);
-    R.a_yx = static_cast<float>(th[1]);
-    R.a_xy = static_cast<float>(th[3]);
-    R.a_xx = static_cast<float>(th[4]);
-    R.fy = static_cast<float>(p0y - by);
-    R.fx = static_cast<float>(p0x - bx);
-    // bases far outside any section saturate (their pixels take the fill value)
-    R.by = static_cast<int>(fmin(fmax(by, -1e9), 1e9));
-    R.bx = static_cast<int>(fmin(fmax(bx, -1e9), 1e9));
-    rec[r] = R;
+  // the tile's first cells (two integer divisions per CTA, shared): the
+  // threads then step from them without dividing
+  __shared__ int tile_cells[4];  // cy0, dy0, cx0, dx0
+  if (threadIdx.x == 0) {
+    auto cell_i = [&](int v, int o, int n) {
+      const int d = v - o;
+      const int c = d >= 0 ? d / mesh.cell : -((-d + mesh.cell - 1) / mesh.cell);
+      return c < 0 ? 0 : (c >= n ? n - 1 : c);
+    };
+    const int cy0 = cell_i(ty0, mesh.origin_y, mesh.ny), cx0 = cell_i(tx0, mesh.origin_x, mesh.nx);
+    tile_cells[0] = cy0;
+    tile_cells[1] = ty0 - (mesh.origin_y + cy0 * mesh.cell);
+    tile_cells[2] = cx0;
+    tile_cells[3] = tx0 - (mesh.origin_x + cx0 * mesh.cell);
   }
   __syncthreads();
   const int tx = threadIdx.x & 31, tyl = threadIdx.x >> 5;
   const int x = tx0 + tx;
   if (x >= out_w) return;
-  const int cx = cell_i(x, mesh.origin_x, mesh.nx);
-  const int dxc = x - (mesh.origin_x + cx * mesh.cell);
+  // cells only advance while the offset reaches the cell side (cell >= 8: at
+  // most 4 steps across the 32-pixel tile), and stay clamped at the last cell
+  int cx = tile_cells[2], dxc = tile_cells[3] + tx;
+  while (dxc >= mesh.cell && cx < mesh.nx - 1) {
+    dxc -= mesh.cell;
+    cx += 1;
+  }
+  int cy = tile_cells[0], dyc = tile_cells[1] + tyl;
+  while (dyc >= mesh.cell && cy < mesh.ny - 1) {
+    dyc -= mesh.cell;
+    cy += 1;
+  }
+  const float fdx = small_int_to_float(dxc);
+  const float cellf = small_int_to_float(mesh.cell);
+  float fdy = small_int_to_float(dyc);
+  // rows y = ty0 + tyl + 8 k: the cell advances at most once per step (cell >= 8)
+  constexpr int K = kTile / 8;
+  // phase 1: records and sample points of the thread's K pixels
+  float4 r0[K], r1[K];
 #pragma unroll
-  for (int k = 0; k < kTile / 8; ++k) {
-    const int y = ty0 + tyl + 8 * k;
-    if (y >= out_h) break;
-    const int cy = cell_i(y, mesh.origin_y, mesh.ny);
-    const int dyc = y - (mesh.origin_y + cy * mesh.cell);
+  for (int k = 0; k < K; ++k) {
+    if (k > 0) {
+      dyc += 8;
+      fdy += 8.0f;
+      if (dyc >= mesh.cell && cy < mesh.ny - 1) {
+        cy += 1;
+        dyc -= mesh.cell;
+        fdy -= cellf;
+      }
+    }
     const int half = dxc >= dyc ? 0 : 1;
-    const RenderRec R = rec[((cy - cy_lo) * ncx + (cx - cx_lo)) * 2 + half];
-    const float fdy = static_cast<float>(dyc), fdx = static_cast<float>(dxc);
-    const float ly = fmaf(R.a_yx, fdx, fmaf(R.a_yy, fdy, R.fy));
-    const float lx = fmaf(R.a_xx, fdx, fmaf(R.a_xy, fdy, R.fx));
-    const float fly = floorf(ly), flx = floorf(lx);
-    long long iy = static_cast<long long>(R.by) + static_cast<long long>(fly);
-    long long ix = static_cast<long long>(R.bx) + static_cast<long long>(flx);
-    float fy = ly - fly, fx = lx - flx;
+    const float4* rp = reinterpret_cast<const float4*>(rec + (2 * (cy * mesh.nx + cx) + half));
+    r0[k] = __ldg(rp);      // (a_yy, a_yx, a_xy, a_xx)
+    r1[k] = __ldg(rp + 1);  // (fy, fx, by, bx)
+    r1[k].x = fmaf(r0[k].y, fdx, fmaf(r0[k].x, fdy, r1[k].x));  // local sample point
+    r1[k].y = fmaf(r0[k].w, fdx, fmaf(r0[k].z, fdy, r1[k].y));
+  }
+  int yi[K], xi[K];
+  float fyv[K], fxv[K];
+  bool ins[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float ly = fminf(fmaxf(r1[k].x, -4e6f), 4e6f);  // |sum with the base| < 2^31; NaN -> outside
+    const float lx = fminf(fmaxf(r1[k].y, -4e6f), 4e6f);
+    float fy, fx;
+    int iy = __float_as_int(r1[k].z) + floor_frac(ly, fy);
+    int ix = __float_as_int(r1[k].w) + floor_frac(lx, fx);
     // inside [0, h-1] x [0, w-1]
     const bool inside = iy >= 0 && ix >= 0 && (iy < src_h - 1 || (iy == src_h - 1 && fy == 0.f)) &&
                         (ix < src_w - 1 || (ix == src_w - 1 && fx == 0.f));
-    float v = fill;
-    if (inside) {
-      if (iy == src_h - 1) {
-        iy -= 1;
-        fy = 1.f;
-      }
-      if (ix == src_w - 1) {
-        ix -= 1;
-        fx = 1.f;
-      }
-      const int yi = static_cast<int>(iy), xi = static_cast<int>(ix);
-      const float s00 = src_px(src, src_pitch, yi, xi), s01 = src_px(src, src_pitch, yi, xi + 1);
-      const float s10 = src_px(src, src_pitch, yi + 1, xi), s11 = src_px(src, src_pitch, yi + 1, xi + 1);
-      const float top = fmaf(fx, s01 - s00, s00), bot = fmaf(fx, s11 - s10, s10);
-      v = fmaf(fy, bot - top, top);
+    if (iy == src_h - 1) {
+      iy -= 1;
+      fy = 1.f;
     }
-    out[static_cast<long long>(y) * out_pitch + x] = v;
+    if (ix == src_w - 1) {
+      ix -= 1;
+      fx = 1.f;
+    }
+    ins[k] = inside;
+    yi[k] = inside ? iy : 0;  // outside pixels read the (valid) corner and take the fill value
+    xi[k] = inside ? ix : 0;
+    fyv[k] = fy;
+    fxv[k] = fx;
+  }
+  // phase 2: all source loads in flight together
+  float sv[K][4];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const TIn* s0 = src + (static_cast<IDX>(yi[k]) * src_pitch + xi[k]);
+    sv[k][0] = src_val(s0);
+    sv[k][1] = src_val(s0 + 1);
+    sv[k][2] = src_val(s0 + src_pitch);
+    sv[k][3] = src_val(s0 + src_pitch + 1);
+  }
+  // phase 3: interpolate and store
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int y = ty0 + tyl + 8 * k;
+    const float top = fmaf(fxv[k], sv[k][1] - sv[k][0], sv[k][0]);
+    const float bot = fmaf(fxv[k], sv[k][3] - sv[k][2], sv[k][2]);
+    const float v = ins[k] ? fmaf(fyv[k], bot - top, top) : fill;
+    if (y < out_h) __stcs(out + (static_cast<IDX>(y) * out_pitch + x), v);
   }
 }
 
@@ -327,28 +415,62 @@ extern "C" swift_status swift_mesh_fit(const float* q, const float* p, const flo
   if (n_points > 0 && (!q || !p || !w)) return SWIFT_ERR_INVALID_ARG;
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   const long long T = 2ll * mesh->ny * mesh->nx;
-  swift::mesh_fit_kernel<<<static_cast<unsigned>(T), swift::kFitThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  swift::mesh_fit_kernel<<<static_cast<unsigned>(T), swift::kMeshFitThreads, 0,
+                           static_cast<cudaStream_t>(stream)>>>(
       q, p, w, n_points, *mesh, band, theta, status);
   return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
 }
 
-extern "C" swift_status swift_render(const swift_image* src, swift_dtype dtype, const double* theta,
+extern "C" swift_status swift_render_prepare(const double* theta, const swift_mesh* mesh, void* records,
+                                             void* stream) {
+  if (!swift::mesh_ok(mesh) || !theta || !records || (reinterpret_cast<uintptr_t>(records) & 15) != 0)
+    return SWIFT_ERR_INVALID_ARG;
+  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  const int T = 2 * mesh->ny * mesh->nx;
+  swift::render_prepare_kernel<<<(T + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      theta, *mesh, static_cast<swift::RenderRec*>(records), T);
+  return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
+}
+
+extern "C" swift_status swift_render(const swift_image* src, swift_dtype dtype, const void* records,
                                      const swift_mesh* mesh, float* out, int32_t out_h, int32_t out_w,
                                      int64_t out_pitch, float fill, void* stream) {
   if (!src || !src->data || src->height < 2 || src->width < 2 || src->pitch < src->width) return SWIFT_ERR_INVALID_ARG;
   if (dtype != SWIFT_IN_U8 && dtype != SWIFT_IN_F32) return SWIFT_ERR_INVALID_ARG;
-  if (!swift::mesh_ok(mesh) || !theta || !out || out_h < 0 || out_w < 0 || out_pitch < out_w) return SWIFT_ERR_INVALID_ARG;
+  if (!swift::mesh_ok(mesh) || !records || (reinterpret_cast<uintptr_t>(records) & 15) != 0 || !out || out_h < 0 ||
+      out_w < 0 || out_pitch < out_w)
+    return SWIFT_ERR_INVALID_ARG;
   if (out_h == 0 || out_w == 0) return SWIFT_OK;
+  // pixel offsets from their cell stay below 2^22 (small-integer float conversion)
+  if (out_h > (1 << 20) || out_w > (1 << 20) || llabs(static_cast<long long>(mesh->origin_y)) > (1 << 20) ||
+      llabs(static_cast<long long>(mesh->origin_x)) > (1 << 20) ||
+      static_cast<long long>(mesh->cell) * (mesh->ny > mesh->nx ? mesh->ny : mesh->nx) > (1 << 20))
+    return SWIFT_ERR_INVALID_ARG;
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   const dim3 grid((out_w + swift::kTile - 1) / swift::kTile, (out_h + swift::kTile - 1) / swift::kTile);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (dtype == SWIFT_IN_U8)
-    swift::render_kernel<uint8_t><<<grid, 256, 0, st>>>(static_cast<const uint8_t*>(src->data), src->pitch,
-                                                          src->height, src->width, theta, *mesh, out, out_pitch,
-                                                          out_h, out_w, fill);
-  else
-    swift::render_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(src->data), src->pitch, src->height,
-                                                        src->width, theta, *mesh, out, out_pitch, out_h, out_w, fill);
+  const swift::RenderRec* rec = static_cast<const swift::RenderRec*>(records);
+  const bool small = static_cast<long long>(src->height) * src->pitch < (1ll << 31) &&
+                     static_cast<long long>(out_h) * out_pitch < (1ll << 31);
+  if (dtype == SWIFT_IN_U8) {
+    const uint8_t* s8 = static_cast<const uint8_t*>(src->data);
+    if (small)
+      swift::render_kernel<uint8_t, int><<<grid, 256, 0, st>>>(s8, static_cast<int>(src->pitch), src->height,
+                                                               src->width, rec, *mesh, out,
+                                                               static_cast<int>(out_pitch), out_h, out_w, fill);
+    else
+      swift::render_kernel<uint8_t, long long><<<grid, 256, 0, st>>>(s8, src->pitch, src->height, src->width, rec,
+                                                                     *mesh, out, out_pitch, out_h, out_w, fill);
+  } else {
+    const float* sf = static_cast<const float*>(src->data);
+    if (small)
+      swift::render_kernel<float, int><<<grid, 256, 0, st>>>(sf, static_cast<int>(src->pitch), src->height,
+                                                             src->width, rec, *mesh, out, static_cast<int>(out_pitch),
+                                                             out_h, out_w, fill);
+    else
+      swift::render_kernel<float, long long><<<grid, 256, 0, st>>>(sf, src->pitch, src->height, src->width, rec,
+                                                                   *mesh, out, out_pitch, out_h, out_w, fill);
+  }
   return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
 }
 

@@ -79,6 +79,8 @@ def test_mir_argument_errors_before_any_launch():
     assert lib.swift_mesh_fit(dummy, dummy, dummy, 1, C.byref(bad), 0, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_mesh_fit(dummy, dummy, dummy, 1, C.byref(good), -1, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_mesh_fit(None, None, None, 1, C.byref(good), 0, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_render_prepare(dummy, C.byref(bad), dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_render_prepare(dummy, C.byref(good), C.c_void_p(8), None) == _lib.SWIFT_ERR_INVALID_ARG
     img = _lib.SwiftImage(None, 8, 0, 8, 8, 1)
     assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 8, 8, 8, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
     img = _lib.SwiftImage(16, 8, 0, 8, 8, 1)
