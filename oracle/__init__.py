@@ -6,3 +6,4 @@ and the CPU-baseline leg of ``bench.py``; never by the library.
 from .swim import *  # noqa: F401,F403
 from . import swim  # noqa: F401
 from . import mir  # noqa: F401
+from . import remod  # noqa: F401
