@@ -18,6 +18,8 @@ Other workloads (``--workload``):
   mir         the rendering step: per-triangle affine fit to the SNR-weighted swim
               correspondences of the headline grid and texture mapping of the 4096^2
               moving section (metric: output pixels/s)
+  remod       the model and pyramid steps: Z-averaged model of every section of a
+              9-section 4096^2 stack and its 2x / 4x box-mean levels (metric: sections/s)
 
 All inputs are seeded synthetic stand-ins for the paper's ssEM sections
 (``synth``).  Timing: W warm-up steps, then K timed steps; L2 is flushed (256 MiB
@@ -728,6 +730,116 @@ def mir_main(args, torch, swift, dev, world, rank):
         print(json.dumps(line))
 
 
+REMOD_METRIC = "sections/sec (remod: Z-averaged model of every section + iscale 2x/4x pyramid)"
+
+
+def remod_main(args, torch, swift, dev, world, rank):
+    """Workload: a 9-section stack of 4096^2 uint8 EM-like sections (the
+    headline section drifting by one pixel per section, independent noise);
+    a step computes the Z model of every section (k = 4, section 6 marked
+    damaged) and the 2x and 4x box-mean pyramid levels of every section.
+    Metric: sections per second."""
+    import synth
+    size, Z, k = 4096, 9, 4
+    a, _ = synth.em_section_pair(size)
+    rng = np.random.default_rng(90)
+    stack = np.stack([np.clip(np.roll(a, (z, -z), (0, 1)).astype(np.int16)
+                              + rng.integers(-6, 7, a.shape, dtype=np.int16), 0, 255).astype(np.uint8)
+                      for z in range(Z)])
+    ts = torch.from_numpy(stack).to(dev)
+    valid = torch.ones(Z, dtype=torch.uint8, device=dev)
+    valid[6] = 0
+    model = torch.empty((Z, size, size), dtype=torch.float32, device=dev)
+    p2 = torch.empty((Z, size // 2, size // 2), dtype=torch.uint8, device=dev)
+    p4 = torch.empty((Z, size // 4, size // 4), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        swift.zmodel(ts, k, valid=valid, out=model, stream=stream)
+        swift.downsample(ts, 2, out=p2, stream=stream)
+        swift.downsample(ts, 4, out=p4, stream=stream)
+
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank())
+    sampler.start()
+    time.sleep(0.3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    for e0, e1, e2 in ev:
+        flush.zero_()
+        e0.record(stream)
+        swift.zmodel(ts, k, valid=valid, out=model, stream=stream)
+        e1.record(stream)
+        swift.downsample(ts, 2, out=p2, stream=stream)
+        swift.downsample(ts, 4, out=p4, stream=stream)
+        e2.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(e0.elapsed_time(e2) for e0, _, e2 in ev)
+    zm_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
+    ds_ms = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / args.steps
+    total_ms, value = aggregate_over_ranks(total_ms, Z, args.steps, world, dev)
+    print(f"[bench] remod rank {rank}: {args.steps} steps, {total_ms / args.steps:.4f} ms/step "
+          f"(zmodel {zm_ms:.4f}, pyramid {ds_ms:.4f}), {value:.1f} sections/s", file=sys.stderr, flush=True)
+
+    hs = torch.from_numpy(stack).pin_memory()
+    hm = torch.empty((Z, size, size), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ts.copy_(hs, non_blocking=True)
+        step()
+        hm.copy_(model, non_blocking=True)
+        stream.synchronize()
+    e2e_value = world * Z * e2e_steps / (time.perf_counter() - t0)
+
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    px = size * size
+    algo_bytes = Z * px * (1 + 4)  # each section read once, each model written (float32)
+    achieved = algo_bytes / (zm_ms / 1e3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import remod as orm
+        rows = 256  # a band of rows of every section
+        t0 = time.perf_counter()
+        orm.zmodel(stack[:, :rows], k, valid.cpu().numpy().astype(bool))
+        for z in range(Z):
+            orm.downsample(stack[z, :rows // 4 * 4, :256], 4)
+        dt = time.perf_counter() - t0
+        cpu = {"value": Z * rows / size / dt, "unit": "sections/s", "cores": 1, "kind": "oracle",
+               "sample": f"Z models of the first {rows} of {size} rows of all {Z} sections plus a 4x pyramid "
+                         f"block, numpy, one process ({dt:.2f} s), scaled to whole sections"}
+    line = {
+        "metric": REMOD_METRIC, "value": value, "unit": "sections/s", "n_gpus": world, "steps": args.steps,
+        "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8 in, f32 model", "data": "synthetic",
+        "config": {"workload": f"{Z}-section {size}x{size} uint8 stack; Z model (k = {k}, one damaged section) "
+                               f"and 2x / 4x pyramid levels of every section",
+                   "name": "remod", "zmodel_ms": zm_ms, "pyramid_ms": ds_ms,
+                   "l2": "flushed before every timed step (256 MiB write, outside the step's events)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "zmodel_kernel<4>",
+                     "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); algorithmic bytes = 1 B "
+                                  "read + 4 B written per section pixel"},
+        "e2e": {"value": e2e_value, "unit": "sections/s", "h2d_bytes_per_step": int(stack.nbytes),
+                "d2h_bytes_per_step": int(Z * px * 4)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def local_rank() -> int:
     return int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -796,7 +908,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sections",
-                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "mir"])
+                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "mir", "remod"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2", "fp16x2"])
     ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (sections workload)")
     ap.add_argument("--windows", type=int, default=0, help="limit the windows per step (small profiling cases)")
@@ -820,8 +932,8 @@ def main():
     torch.cuda.set_device(dev)
     import paper_1612_04787_gb300 as swift
 
-    if args.workload == "mir":
-        mir_main(args, torch, swift, dev, world, rank)
+    if args.workload in ("mir", "remod"):
+        (mir_main if args.workload == "mir" else remod_main)(args, torch, swift, dev, world, rank)
         if world > 1:
             dist.destroy_process_group()
         return

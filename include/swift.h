@@ -349,6 +349,34 @@ swift_status swift_render_prepare(const double* theta, const swift_mesh* mesh, v
 swift_status swift_render(const swift_image* src, swift_dtype dtype, const void* records, const swift_mesh* mesh,
                           float* out, int32_t out_h, int32_t out_w, int64_t out_pitch, float fill, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Pyramid and model steps around the match ("iscale" and "remod", Sec. III
+ * module list and model averaging).
+ * ------------------------------------------------------------------------ */
+
+/* Box-mean downsampling by an integer factor (1..64): out (y, x) is the mean
+ * of the factor x factor block at (factor y, factor x); partial edge blocks
+ * are dropped, so out is floor(H / f) x floor(W / f) (rows <= 65535, else
+ * SWIFT_ERR_UNSUPPORTED).  uint8: exact integer mean rounded half to even;
+ * float32: float32 block sum in row-major order divided by f^2.  out has the
+ * source's type, device memory, out_pitch elements per row.  A source with
+ * count > 1 is a batch of images `stride` elements apart, downsampled in one
+ * launch into consecutive output planes of out_pitch x floor(H / f)
+ * elements. */
+swift_status swift_downsample(const swift_image* src, swift_dtype dtype, int32_t factor, void* out, int64_t out_pitch,
+                              void* stream);
+
+/* Z-averaged models of a uint8 section stack (device: section j at
+ * stack + j * stride, rows `pitch` bytes apart): out[z] (float32, device, at
+ * out + z * out_stride, rows out_pitch floats apart) is the mean of the
+ * sections j in [z - k, z + k], j != z, with valid[j] != 0 (valid: device
+ * uint8 [n_sections], NULL = all valid); with no such section it is section z
+ * itself.  out = float32(integer sum) / float32(count), one IEEE division.
+ * height <= 65535. */
+swift_status swift_zmodel(const uint8_t* stack, int64_t stride, int32_t n_sections, int32_t height, int32_t width,
+                          int64_t pitch, int32_t k, const uint8_t* valid, float* out, int64_t out_stride,
+                          int64_t out_pitch, void* stream);
+
 /* Set the whitening exponent of one level for later calls (w in [0, 1]). */
 swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w);
 

@@ -24,7 +24,7 @@ from ._lib import (APOD, DTYPE, PRECISION, SwiftBatch, SwiftImage, SwiftLevel, S
                    lib)
 
 __all__ = ["Level", "Plan", "decode", "SwiftError", "version", "match_warped", "WIN_OK", "WIN_OUT_OF_BOUNDS",
-           "WIN_FLAT", "WIN_NONFINITE", "Mesh", "correspondences", "fit_affine", "mesh_fit", "render", "render_records",
+           "WIN_FLAT", "WIN_NONFINITE", "Mesh", "correspondences", "fit_affine", "mesh_fit", "render", "render_records", "downsample", "zmodel",
            "FIT_OK", "FIT_FALLBACK", "FIT_DEGENERATE"]
 
 
@@ -378,4 +378,50 @@ def render(src, theta, mesh: Mesh, out_h: int, out_w: int, fill: float = 0.0, ou
     check(lib.swift_render(C.byref(img), DTYPE["u8" if src.dtype == torch.uint8 else "f32"], records.data_ptr(),
                            C.byref(mc), out.data_ptr(), int(out_h), int(out_w), out.stride(0), float(fill),
                            _stream_ptr(stream)), "swift_render")
+    return out
+
+
+# --------------------------------------------------------------------------- #
+# pyramid (iscale) and Z-model (remod)
+# --------------------------------------------------------------------------- #
+def downsample(img, factor: int, out=None, stream=None):
+    """f x f box-mean downsampling of a [H, W] (or a batch [N, H, W]) uint8 /
+    float32 CUDA image (uint8: exact mean rounded half to even).  Returns
+    [H // f, W // f] (or [N, H // f, W // f])."""
+    if img.dtype not in (torch.uint8, torch.float32) or img.dim() not in (2, 3) or not img.is_cuda:
+        raise TypeError("img must be a [H, W] or [N, H, W] uint8 or float32 CUDA tensor")
+    if img.stride(-1) != 1:
+        raise ValueError("image rows must be contiguous")
+    batch = img.dim() == 3
+    N = img.shape[0] if batch else 1
+    H, W = img.shape[-2] // factor, img.shape[-1] // factor
+    shape = (N, H, W) if batch else (H, W)
+    if out is None:
+        out = torch.empty(shape, dtype=img.dtype, device=img.device)
+    elif out.dtype != img.dtype or tuple(out.shape) != shape or not out.is_contiguous():
+        raise ValueError("out must be a contiguous tensor of the downsampled size and type")
+    im = SwiftImage(img.data_ptr(), img.stride(-2), img.stride(0) if batch else 0, img.shape[-2], img.shape[-1], N)
+    check(lib.swift_downsample(C.byref(im), DTYPE["u8" if img.dtype == torch.uint8 else "f32"], int(factor),
+                               out.data_ptr(), W, _stream_ptr(stream)), "swift_downsample")
+    return out
+
+
+def zmodel(stack, k: int, valid=None, out=None, stream=None):
+    """Z-averaged models (float32 [Z, H, W]) of a uint8 [Z, H, W] CUDA stack:
+    the mean of the valid sections within +-k, the section itself excluded."""
+    if stack.dtype != torch.uint8 or stack.dim() != 3 or not stack.is_cuda or stack.stride(2) != 1:
+        raise TypeError("stack must be a [Z, H, W] uint8 CUDA tensor with contiguous rows")
+    Z, H, W = stack.shape
+    if out is None:
+        out = torch.empty((Z, H, W), dtype=torch.float32, device=stack.device)
+    elif out.dtype != torch.float32 or tuple(out.shape) != (Z, H, W) or out.stride(2) != 1:
+        raise ValueError("out must be a float32 [Z, H, W] tensor with contiguous rows")
+    vptr = None
+    if valid is not None:
+        valid = valid.to(device=stack.device, dtype=torch.uint8).contiguous()
+        if valid.numel() != Z:
+            raise ValueError("valid must have one flag per section")
+        vptr = valid.data_ptr()
+    check(lib.swift_zmodel(stack.data_ptr(), stack.stride(0), Z, H, W, stack.stride(1), int(k), vptr,
+                           out.data_ptr(), out.stride(0), out.stride(1), _stream_ptr(stream)), "swift_zmodel")
     return out

@@ -48,6 +48,8 @@ EXPORTS = (
     "swift_mesh_fit",
     "swift_render_prepare",
     "swift_render",
+    "swift_downsample",
+    "swift_zmodel",
 )
 
 FIT_OK, FIT_FALLBACK, FIT_DEGENERATE = 0, 1, 2
@@ -134,6 +136,11 @@ def _load():
     lib.swift_render.argtypes = [C.POINTER(SwiftImage), C.c_int, C.c_void_p, C.POINTER(SwiftMesh), C.c_void_p,
                                  C.c_int32, C.c_int32, C.c_int64, C.c_float, C.c_void_p]
     lib.swift_render.restype = C.c_int
+    lib.swift_downsample.argtypes = [C.POINTER(SwiftImage), C.c_int, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]
+    lib.swift_downsample.restype = C.c_int
+    lib.swift_zmodel.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32,
+                                 C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
+    lib.swift_zmodel.restype = C.c_int
     return lib
 
 
