@@ -74,7 +74,8 @@ enum {
 };
 
 /* One matching configuration (one pyramid level), Sec. III:
- *   n                    window side; 64, 128 or 256 (power of two)
+ *   n                    window side; 64, 128, 256 or 512 (512: streaming
+ *                        schedule, FP32, unwarped forward only)
  *   whiten_exponent      w in [0, 1]: magnitudes of the cross-power spectrum
  *                        C = M conj(R) are raised to 1 - w (G = C |C|^-w);
  *                        0 = plain correlation, 1 = phase-only correlation
@@ -199,8 +200,9 @@ swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_
  * must be NULL); it runs the same streaming kernels and gives the same
  * results.
  *
- * Limits: at most floor((24 MiB - 5120 B) / per-window bytes) windows per
- * call: 31 windows of 256 x 256, 127 of 128 x 128, 511 of 64 x 64.  Larger
+ * Limits: at most floor((24 MiB - 9216 B) / per-window bytes) windows per
+ * call: 7 windows of 512 x 512, 31 of 256 x 256, 127 of 128 x 128, 511 of
+ * 64 x 64.  Larger
  * batches return SWIFT_ERR_CAPACITY before any work is queued; split them.
  *
  * Set-up: the first call on each device looks up the array's device address

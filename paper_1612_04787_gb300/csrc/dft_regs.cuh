@@ -114,11 +114,45 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = o[i];
 }
 
+// cos / sin of e * pi / 16, e = 0..15 (the twiddles W32^e)
+__device__ constexpr float kC32[16] = {
+    1.0f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f,
+    0.70710678118654752f, 0.55557023301960218f, 0.38268343236508978f, 0.19509032201612826f,
+    0.0f, -0.19509032201612826f, -0.38268343236508978f, -0.55557023301960218f,
+    -0.70710678118654752f, -0.83146961230254524f, -0.92387953251128674f, -0.98078528040323043f};
+__device__ constexpr float kS32[16] = {
+    0.0f, 0.19509032201612826f, 0.38268343236508978f, 0.55557023301960218f,
+    0.70710678118654752f, 0.83146961230254524f, 0.92387953251128674f, 0.98078528040323043f,
+    1.0f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f,
+    0.70710678118654752f, 0.55557023301960218f, 0.38268343236508978f, 0.19509032201612826f};
+
+// 32-point DFT: even / odd 16-point halves, then X[k] = E[k] + W^k O[k],
+// X[k + 16] = E[k] - W^k O[k] with W = exp(DIR 2 pi i / 32)
+template <int DIR>
+__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft16<DIR>(e);
+  dft16<DIR>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float c = kC32[k], sn = DIR * kS32[k];
+    const float2 t = k == 0 ? o[k] : make_float2(fmaf(c, o[k].x, -sn * o[k].y), fmaf(c, o[k].y, sn * o[k].x));
+    v[k] = cadd(e[k], t);
+    v[k + 16] = csub(e[k], t);
+  }
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
-  if constexpr (R == 16) dft16<DIR>(v);
+  if constexpr (R == 32) dft32<DIR>(v);
+  else if constexpr (R == 16) dft16<DIR>(v);
   else if constexpr (R == 8) dft8<DIR>(v);
-  else static_assert(R == 8 || R == 16, "radix");
+  else static_assert(R == 8 || R == 16 || R == 32, "radix");
 }
 
 }  // namespace swift

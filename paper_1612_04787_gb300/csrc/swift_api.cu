@@ -13,13 +13,16 @@ namespace {
 
 constexpr int kMaxLevels = 8;
 constexpr int kTimingSets = 1024;
-constexpr int kSizes[3] = {64, 128, 256};
+constexpr int kNumSizes = 4;
+constexpr int kSizes[kNumSizes] = {64, 128, 256, 512};
 
 int size_slot(int n) {
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < kNumSizes; ++i)
     if (kSizes[i] == n) return i;
   return -1;
 }
+// window sizes with a fused (cluster) kernel; 512 x 512 windows always stream
+bool has_fused(int n) { return n <= 256; }
 
 // 1D taper in FP64 (Sec. III: cosine taper).  Periodic convention: Hann is
 // a[k] = (1 - cos(2 pi k / n)) / 2; Tukey(alpha) has raised-cosine ramps of
@@ -52,9 +55,9 @@ struct swift_plan_s {
   int device = 0;
   float* taper[kMaxLevels] = {};
   double inv_sum_a[kMaxLevels] = {};
-  float2* twiddle[3] = {};
+  float2* twiddle[kNumSizes] = {};
   // tensor-core precision variant: fragment and twiddle tables per window size
-  void* tc_tab[3] = {};
+  void* tc_tab[kNumSizes] = {};
   // streaming forward path: per-level choice and its workspace
   int stream_level[kMaxLevels] = {};
   void* work = nullptr;
@@ -94,7 +97,7 @@ static swift_status release(swift_plan p) {
   if (cur != p->device) cudaSetDevice(p->device);
   for (int l = 0; l < kMaxLevels; ++l)
     if (p->taper[l]) cudaFree(p->taper[l]);
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < kNumSizes; ++i) {
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
     if (p->tc_tab[i]) cudaFree(p->tc_tab[i]);
   }
@@ -142,8 +145,8 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
     delete p;
     return SWIFT_ERR_CUDA;
   }
-  double a[256];
-  float af[256];
+  double a[512];
+  float af[512];
   for (int l = 0; l < n_levels; ++l) {
     const int n = levels[l].n;
     taper_table(n, levels[l].apod, levels[l].tukey_alpha, a);
@@ -163,8 +166,8 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
     const int slot = size_slot(n);
     if (!p->twiddle[slot]) {
       int r1 = 0, r2 = 0;
-      swift::forward_radices(n, &r1, &r2);
-      float2 tw[256];
+      swift::stream_radices(n, &r1, &r2);
+      float2 tw[512];
       for (int m = 0; m < r2; ++m)
         for (int j = 0; j < r1; ++j) {
           const int e = (j * m) % n;
@@ -393,6 +396,8 @@ static swift_status ensure_bwork(swift_plan plan) {
 static swift_status check_warp_batch(swift_plan plan, const swift_batch* batch) {
   if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
   if (plan->prec != SWIFT_PREC_FP32) return SWIFT_ERR_UNSUPPORTED;  // warp / backward are FP32 only
+  for (int l = 0; l < plan->n_levels; ++l)
+    if (plan->levels[l].n > 256) return SWIFT_ERR_UNSUPPORTED;  // warp / backward are built up to 256 x 256
   const int64_t B = batch->n_windows;
   if (B < 0 || B > plan->max_windows) return SWIFT_ERR_INVALID_ARG;
   if (B == 0) return SWIFT_OK;
@@ -461,6 +466,7 @@ extern "C" swift_status swift_plan_set_schedule(swift_plan plan, int32_t level, 
   if (schedule == SWIFT_SCHED_DEFAULT) {
     plan->stream_level[level] = default_stream(plan->levels[level].n) ? 1 : 0;
   } else if (schedule == SWIFT_SCHED_FUSED || schedule == SWIFT_SCHED_STREAM) {
+    if (schedule == SWIFT_SCHED_FUSED && !has_fused(plan->levels[level].n)) return SWIFT_ERR_UNSUPPORTED;
     plan->stream_level[level] = schedule == SWIFT_SCHED_STREAM ? 1 : 0;
   } else {
     return SWIFT_ERR_INVALID_ARG;
@@ -487,7 +493,7 @@ extern "C" swift_status swift_plan_autotune(swift_plan plan, const swift_batch* 
   for (int l = 0; l < used && e == SWIFT_OK; ++l) {
     float best = 3.4e38f;
     int best_sched = plan->stream_level[l];
-    for (int sched = 0; sched < 2 && e == SWIFT_OK; ++sched) {
+    for (int sched = has_fused(plan->levels[l].n) ? 0 : 1; sched < 2 && e == SWIFT_OK; ++sched) {
       plan->stream_level[l] = sched;
       if ((e = run_level(plan, batch, l, out, st)) != SWIFT_OK) break;  // warm-up
       cudaEventRecord(e0, st);

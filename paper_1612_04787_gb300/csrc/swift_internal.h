@@ -103,6 +103,8 @@ cudaError_t launch_wout(const double* acc, float* out, int n, cudaStream_t strea
 // base pointers, pitches and widths, and a single reference section)
 cudaError_t launch_forward(int n, swift_dtype dtype, bool bulk, const MatchLaunch& L, cudaStream_t stream);
 // radix split (R1, R2) used by the kernel for window size n; false if n is not built
+// radices (R1, R2) of the streaming kernels' 1D transforms, n = R1 R2
+bool stream_radices(int n, int* r1, int* r2);
 bool forward_radices(int n, int* r1, int* r2);
 
 }  // namespace swift

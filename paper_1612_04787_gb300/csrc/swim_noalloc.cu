@@ -19,7 +19,7 @@ namespace {
 
 // Static scratch shared by every call on a device (held until the process exits).
 constexpr size_t kNoAllocBytes = 24u << 20;  // 24 MiB
-constexpr size_t kTableBytes = 4096;         // taper (n floats) + twiddles (n complex)
+constexpr size_t kTableBytes = 8192;         // taper (n floats, at 0) + twiddles (n complex, at 2048)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of the array, looked up once per device with that device
@@ -64,7 +64,7 @@ extern "C" swift_status swift_match_batch_noalloc(const swift_level* level, swif
                                                   swift_result* out, void* stream) {
   if (!level || !batch) return SWIFT_ERR_INVALID_ARG;
   const swift_level lv = *level;
-  if (lv.n != 64 && lv.n != 128 && lv.n != 256) return SWIFT_ERR_UNSUPPORTED;
+  if (lv.n != 64 && lv.n != 128 && lv.n != 256 && lv.n != 512) return SWIFT_ERR_UNSUPPORTED;
   if (in != SWIFT_IN_U8 && in != SWIFT_IN_F32) return SWIFT_ERR_INVALID_ARG;
   if (!(lv.whiten_exponent >= 0.f && lv.whiten_exponent <= 1.f)) return SWIFT_ERR_INVALID_ARG;
   if (lv.apod != SWIFT_APOD_NONE && lv.apod != SWIFT_APOD_HANN && lv.apod != SWIFT_APOD_TUKEY)
@@ -100,18 +100,18 @@ extern "C" swift_status swift_match_batch_noalloc(const swift_level* level, swif
 
   // tables: taper then twiddles W_n^{j m} = exp(-2 pi i j m / n) stored [m][j]
   const int n = lv.n;
-  double a[256];
+  double a[512];
   taper_values(n, lv.apod, lv.tukey_alpha, a);
   double sum_a = 0.0;
   unsigned char host_tables[kTableBytes];
   float* tap = reinterpret_cast<float*>(host_tables);
-  float2* tw = reinterpret_cast<float2*>(host_tables + 1024);
+  float2* tw = reinterpret_cast<float2*>(host_tables + 2048);
   for (int k = 0; k < n; ++k) {
     sum_a += a[k];
     tap[k] = static_cast<float>(a[k]);
   }
   int r1 = 0, r2 = 0;
-  swift::forward_radices(n, &r1, &r2);
+  swift::stream_radices(n, &r1, &r2);
   for (int m = 0; m < r2; ++m)
     for (int j = 0; j < r1; ++j) {
       const double ang = -2.0 * M_PI * ((j * m) % n) / n;
@@ -143,7 +143,7 @@ extern "C" swift_status swift_match_batch_noalloc(const swift_level* level, swif
   L.radius2 = static_cast<float>(floor(static_cast<double>(lv.snr_exclusion_radius) * lv.snr_exclusion_radius));
   L.inv_sum_a = 1.0 / (sum_a * sum_a);
   L.taper = reinterpret_cast<const float*>(base);
-  L.twiddle = reinterpret_cast<const float2*>(base + 1024);
+  L.twiddle = reinterpret_cast<const float2*>(base + 2048);
   L.out = out;
   const swift::StreamWork W = swift::stream_carve(base + kTableBytes, capacity_for(n), n, 0, B);
   if (swift::launch_stream(n, in, L, W, st) != cudaSuccess) return SWIFT_ERR_CUDA;

@@ -18,6 +18,8 @@ size_t blocks3(int n) {
       return StreamGeom<64>::NB3;
     case 128:
       return StreamGeom<128>::NB3;
+    case 512:
+      return StreamGeom<512>::NB3;
     default:
       return StreamGeom<256>::NB3;
   }
@@ -75,6 +77,25 @@ StreamWork stream_carve(void* base, long long capacity, int n, long long b0, lon
   return W;
 }
 
+bool stream_radices(int n, int* r1, int* r2) {
+  switch (n) {
+    case 64:
+      *r1 = StreamGeom<64>::R1, *r2 = StreamGeom<64>::R2;
+      return true;
+    case 128:
+      *r1 = StreamGeom<128>::R1, *r2 = StreamGeom<128>::R2;
+      return true;
+    case 256:
+      *r1 = StreamGeom<256>::R1, *r2 = StreamGeom<256>::R2;
+      return true;
+    case 512:
+      *r1 = StreamGeom<512>::R1, *r2 = StreamGeom<512>::R2;
+      return true;
+    default:
+      return false;
+  }
+}
+
 cudaError_t launch_stream(int n, swift_dtype dtype, const MatchLaunch& L, const StreamWork& W, cudaStream_t st) {
   const bool u8 = dtype == SWIFT_IN_U8;
   switch (n) {
@@ -84,6 +105,8 @@ cudaError_t launch_stream(int n, swift_dtype dtype, const MatchLaunch& L, const 
       return u8 ? launch_n<128, uint8_t>(L, W, st) : launch_n<128, float>(L, W, st);
     case 256:
       return u8 ? launch_n<256, uint8_t>(L, W, st) : launch_n<256, float>(L, W, st);
+    case 512:
+      return u8 ? launch_n<512, uint8_t>(L, W, st) : launch_n<512, float>(L, W, st);
     default:
       return cudaErrorInvalidValue;
   }

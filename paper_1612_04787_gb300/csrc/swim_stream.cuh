@@ -35,11 +35,11 @@ constexpr int kStatusSkip = -1;  // window of another level: no result written h
 template <int N>
 struct StreamGeom {
   static constexpr int R1 = N == 64 ? 8 : 16;
-  static constexpr int R2 = N / R1;
+  static constexpr int R2 = N / R1;        // 8, 8, 16, 32 for n = 64 .. 512
   static constexpr int T = 256;
-  static constexpr int RS = N == 256 ? 272 : (N == 128 ? 152 : 72);  // padded row stride
+  static constexpr int RS = N == 512 ? 528 : (N == 256 ? 272 : (N == 128 ? 152 : 72));  // padded row stride
   static constexpr int RB = T / R2;        // K1: rows per CTA
-  static constexpr int CB = 16;            // K2: kx values (plus partners) per CTA
+  static constexpr int CB = N == 512 ? 8 : 16;  // K2: kx values (plus partners) per CTA
   static constexpr int NB2 = N / (2 * CB);
   static constexpr int T2 = 2 * CB * R2;   // K2: threads (one pass-A task each)
   static constexpr int PB = (T / R2) < (N / 2) ? (T / R2) : (N / 2);  // K3: row pairs per CTA
@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
 #pragma unroll
   for (int i = 0; i < KB; ++i) {
     const int task = tid + i * T;
+    if ((RB * R1) % T != 0 && task >= RB * R1) break;  // n = 512: 128 tasks for 256 threads
     const int ln = task / R1, k1 = task % R1;
     const float2* row = slab + ln * RS;
     float2 v[R2];
@@ -350,29 +351,19 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [ky][lc], row stride LS
   float2* twid = slab + N * LS;
   for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
-  // gather columns kx(lc) of Zr (rows are contiguous in kx)
+  // column pass A (rows j + R2 m) straight from Zr: consecutive threads take
+  // consecutive lines, i.e. contiguous kx runs of a row (coalesced)
   const float2* zr = W.zr + s * N * N;
-  {
-    constexpr int K = N * LINES / T;
-    const int lc = tid % LINES, ky0 = tid / LINES;
-    const int kx = G::kx_of(cb, lc);
-    float2 q[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) q[i] = __ldcs(zr + (ky0 + i * (T / LINES)) * N + kx);
-#pragma unroll
-    for (int i = 0; i < K; ++i) slab[(ky0 + i * (T / LINES)) * LS + lc] = q[i];
-  }
-  __syncthreads();
-  // column pass A (rows j + R2 m), in place
   constexpr int TA = LINES * R2, TB = LINES * R1;
 #pragma unroll
   for (int i = 0; i < (TA + T - 1) / T; ++i) {
     const int task = tid + i * T;
     if (TA % T != 0 && task >= TA) break;
     const int j = task / LINES, lc = task % LINES;
+    const int kx = G::kx_of(cb, lc);
     float2 v[R1];
 #pragma unroll
-    for (int m = 0; m < R1; ++m) v[m] = slab[(j + R2 * m) * LS + lc];
+    for (int m = 0; m < R1; ++m) v[m] = __ldcs(zr + (j + R2 * m) * N + kx);
     dft<R1, -1>(v);
 #pragma unroll
     for (int q = 0; q < R1; ++q) slab[(j + R2 * q) * LS + lc] = v[q];

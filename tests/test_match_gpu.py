@@ -241,3 +241,28 @@ def test_unaligned_section_width_uses_direct_loads(sections):
     lv = swift.Level(n, 0.65)
     g = run_sections(aw, bw, ro, ro, lv)
     check_sections(aw, bw, ro, ro, lv, g, "width 1001")
+
+
+@pytest.mark.parametrize("w", [0.0, 0.65, 1.0])
+def test_sections_512_parity(w):
+    """512 x 512 windows (streaming schedule, 16 x 32 radix)."""
+    a, b = synth.em_section_pair(1024, seed_content=81, seed_warp=82, seed_noise=(83, 84))
+    ro = np.array([[0, 0], [300, 200], [512, 512], [100, 480]], np.int32)
+    rng = np.random.default_rng(int(10 * w))
+    mo = np.clip(ro + rng.integers(-20, 21, ro.shape), 0, 1024 - 512).astype(np.int32)
+    lv = swift.Level(512, w, "hann", 1.0, 4.0)
+    g = run_sections(a, b, ro, mo, lv)
+    kinds = check_sections(a, b, ro, mo, lv, g, f"512 w={w}")
+    assert kinds.count("exact") >= 3
+
+
+def test_512_schedule_and_warp_limits():
+    plan = swift.Plan([swift.Level(512, 0.65, "hann", 1.0, 3.0)], dtype="u8", max_windows=4)
+    with pytest.raises(swift.SwiftError) as e:
+        plan.set_schedule(0, "fused")
+    assert "UNSUPPORTED" in str(e.value)
+    sec = torch.zeros((1024, 1024), dtype=torch.uint8, device=DEV)
+    org = torch.zeros((2, 2), dtype=torch.int32, device=DEV)
+    with pytest.raises(swift.SwiftError) as e:
+        plan.match(sec, sec, org, org, affine=torch.zeros((2, 6), dtype=torch.float32, device=DEV))
+    assert "UNSUPPORTED" in str(e.value)

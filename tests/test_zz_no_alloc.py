@@ -87,3 +87,22 @@ def test_noalloc_float_patches_and_capacity_limit():
     assert noalloc_match(lv256, "f32", big[:31], big[:31], None, None, out[:31]) == _lib.SWIFT_OK
     torch.cuda.synchronize()
     assert (swift.decode(out[:31])["status"] == swift.WIN_FLAT).all()
+
+
+def test_noalloc_512_matches_plan_path():
+    """512 x 512 windows: 7 fit in the static scratch; results equal the plan path's."""
+    a, b = synth.em_section_pair(1024, seed_content=91, seed_warp=92, seed_noise=(93, 94))
+    ro = np.array([[0, 0], [500, 100], [256, 300]], np.int32)
+    mo = (ro + np.array([[3, -4], [0, 7], [-5, 2]])).clip(0, 512).astype(np.int32)
+    lv = swift.Level(512, 0.65, "hann", 1.0, 3.0)
+    ta, tb = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    tro, tmo = torch.from_numpy(ro).to(DEV), torch.from_numpy(mo).to(DEV)
+    want = swift.decode(swift.Plan([lv], dtype="u8", max_windows=3).match(ta, tb, tro, tmo))
+    for _ in range(2):
+        out = torch.empty((3, 8), dtype=torch.int32, device=DEV)
+        assert noalloc_match(lv, "u8", ta, tb, tro, tmo, out) == _lib.SWIFT_OK
+        torch.cuda.synchronize()
+        assert_close(swift.decode(out), want)
+    big = torch.zeros((8, 512, 512), dtype=torch.float32, device=DEV)
+    out8 = torch.empty((8, 8), dtype=torch.int32, device=DEV)
+    assert noalloc_match(lv, "f32", big, big, None, None, out8) == _lib.SWIFT_ERR_CAPACITY
