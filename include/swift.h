@@ -339,17 +339,19 @@ swift_status swift_mesh_fit(const float* q, const float* p, const float* w, int6
 swift_status swift_render_prepare(const double* theta, const swift_mesh* mesh, void* records, void* stream);
 
 /* Texture-map one source section (src: a uint8 / float32 image, height and
- * width >= 2, pitch in elements) through the mesh into out (device float32
- * [out_h][out_pitch]): output pixel (y, x) belongs to the triangle of its
- * cell (cells clamped to the mesh) and takes the bilinear sample of the
- * source at A (y, x) + t, or `fill` where that point leaves
- * [0, h-1] x [0, w-1].  records from swift_render_prepare with the same mesh.
- * Sample points are an integer base plus an FP32 fraction, so their error
- * stays ~1e-4 px at any section coordinate.  Limits: out_h, out_w, |origin|
- * and the mesh extent (cell x cells) at most 2^20 pixels (else
- * SWIFT_ERR_INVALID_ARG). */
+ * width >= 2, pitch in elements) through the mesh into out (device,
+ * [out_h][out_pitch] elements of out_dtype): output pixel (y, x) belongs to
+ * the triangle of its cell (cells clamped to the mesh) and takes the bilinear
+ * sample of the source at A (y, x) + t, or `fill` where that point leaves
+ * [0, h-1] x [0, w-1].  out_dtype SWIFT_IN_F32 stores the sample;
+ * SWIFT_IN_U8 stores it rounded half to even and clamped to [0, 255].
+ * records from swift_render_prepare with the same mesh.  Sample points are an
+ * integer base plus an FP32 fraction, so their error stays ~1e-4 px at any
+ * section coordinate.  Limits: out_h, out_w, |origin| and the mesh extent
+ * (cell x cells) at most 2^20 pixels (else SWIFT_ERR_INVALID_ARG). */
 swift_status swift_render(const swift_image* src, swift_dtype dtype, const void* records, const swift_mesh* mesh,
-                          float* out, int32_t out_h, int32_t out_w, int64_t out_pitch, float fill, void* stream);
+                          void* out, swift_dtype out_dtype, int32_t out_h, int32_t out_w, int64_t out_pitch,
+                          float fill, void* stream);
 
 /* ------------------------------------------------------------------------
  * Pyramid and model steps around the match ("iscale" and "remod", Sec. III

@@ -7,3 +7,4 @@ from .swim import *  # noqa: F401,F403
 from . import swim  # noqa: F401
 from . import mir  # noqa: F401
 from . import remod  # noqa: F401
+from . import driver  # noqa: F401

@@ -194,3 +194,9 @@ def correspondences(results, ref_origins, mov_origins, n: int, min_snr: float = 
         p[b] = (mov_origins[b][0] + c + (r["sy"] if ok else 0.0), mov_origins[b][1] + c + (r["sx"] if ok else 0.0))
         w[b] = r["snr"] if ok else 0.0
     return q, p, w
+
+
+def to_u8(v):
+    """Rendered values stored as uint8: rounded half to even, clamped to [0, 255]."""
+    v = np.nan_to_num(np.asarray(v, dtype=np.float64), nan=0.0)
+    return np.clip(np.rint(v), 0, 255).astype(np.uint8)

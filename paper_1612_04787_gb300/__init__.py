@@ -363,8 +363,9 @@ def render_records(theta, mesh: Mesh, records=None, stream=None):
 def render(src, theta, mesh: Mesh, out_h: int, out_w: int, fill: float = 0.0, out=None, records=None,
            stream=None):
     """Texture-map ``src`` ([H, W] uint8 / float32 CUDA tensor) through the
-    mesh's triangle affines into a float32 [out_h, out_w] image.  ``records``
-    (from ``render_records``) skips the per-mesh preparation."""
+    mesh's triangle affines into a float32 [out_h, out_w] image (or into
+    ``out``: float32, or uint8 for values rounded half to even and clamped).
+    ``records`` (from ``render_records``) skips the per-mesh preparation."""
     if src.dtype not in (torch.uint8, torch.float32) or src.dim() != 2:
         raise TypeError("src must be a [H, W] uint8 or float32 CUDA tensor")
     img = _image(src, src.dtype, False)
@@ -372,12 +373,13 @@ def render(src, theta, mesh: Mesh, out_h: int, out_w: int, fill: float = 0.0, ou
         records = render_records(theta, mesh, stream=stream)
     if out is None:
         out = torch.empty((out_h, out_w), dtype=torch.float32, device=src.device)
-    elif out.dtype != torch.float32 or out.dim() != 2 or out.shape[0] < out_h or out.stride(1) != 1:
-        raise ValueError("out must be a float32 [out_h, >= out_w] tensor with contiguous rows")
+    elif out.dtype not in (torch.float32, torch.uint8) or out.dim() != 2 or out.shape[0] < out_h or \
+            out.shape[1] < out_w or out.stride(1) != 1:
+        raise ValueError("out must be a float32 or uint8 [>= out_h, >= out_w] tensor with contiguous rows")
     mc = mesh.c()
     check(lib.swift_render(C.byref(img), DTYPE["u8" if src.dtype == torch.uint8 else "f32"], records.data_ptr(),
-                           C.byref(mc), out.data_ptr(), int(out_h), int(out_w), out.stride(0), float(fill),
-                           _stream_ptr(stream)), "swift_render")
+                           C.byref(mc), out.data_ptr(), DTYPE["u8" if out.dtype == torch.uint8 else "f32"],
+                           int(out_h), int(out_w), out.stride(0), float(fill), _stream_ptr(stream)), "swift_render")
     return out
 
 

@@ -134,7 +134,7 @@ def _load():
     lib.swift_render_prepare.argtypes = [C.c_void_p, C.POINTER(SwiftMesh), C.c_void_p, C.c_void_p]
     lib.swift_render_prepare.restype = C.c_int
     lib.swift_render.argtypes = [C.POINTER(SwiftImage), C.c_int, C.c_void_p, C.POINTER(SwiftMesh), C.c_void_p,
-                                 C.c_int32, C.c_int32, C.c_int64, C.c_float, C.c_void_p]
+                                 C.c_int, C.c_int32, C.c_int32, C.c_int64, C.c_float, C.c_void_p]
     lib.swift_render.restype = C.c_int
     lib.swift_downsample.argtypes = [C.POINTER(SwiftImage), C.c_int, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]
     lib.swift_downsample.restype = C.c_int

@@ -259,10 +259,18 @@ __global__ void render_prepare_kernel(const double* theta, swift_mesh mesh, Rend
   rec[t] = R;
 }
 
+// output value: float32 as is; uint8 rounded half to even and clamped to
+// [0, 255] (the 1.5 * 2^23 rounding trick, no conversion instruction)
+__device__ __forceinline__ void store_px(float* p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void store_px(uint8_t* p, float v) {
+  const float c = fminf(fmaxf(v, 0.f), 255.f);  // NaN -> 0
+  *p = static_cast<uint8_t>(__float_as_int(c + 12582912.0f) - 0x4B400000);
+}
+
 // IDX: int for images below 2^31 elements (cheaper address arithmetic), else long long
-template <typename TIn, typename IDX>
+template <typename TIn, typename TOut, typename IDX>
 __global__ void __launch_bounds__(256) render_kernel(const TIn* src, IDX src_pitch, int src_h, int src_w,
-                                                     const RenderRec* rec, swift_mesh mesh, float* out,
+                                                     const RenderRec* rec, swift_mesh mesh, TOut* out,
                                                      IDX out_pitch, int out_h, int out_w, float fill) {
   const int ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
   // the tile's first cells (two integer divisions per CTA, shared): the
@@ -365,7 +373,7 @@ __global__ void __launch_bounds__(256) render_kernel(const TIn* src, IDX src_pit
     const float top = fmaf(fxv[k], sv[k][1] - sv[k][0], sv[k][0]);
     const float bot = fmaf(fxv[k], sv[k][3] - sv[k][2], sv[k][2]);
     const float v = ins[k] ? fmaf(fyv[k], bot - top, top) : fill;
-    if (y < out_h) __stcs(out + (static_cast<IDX>(y) * out_pitch + x), v);
+    if (y < out_h) store_px(out + (static_cast<IDX>(y) * out_pitch + x), v);
   }
 }
 
@@ -432,11 +440,28 @@ extern "C" swift_status swift_render_prepare(const double* theta, const swift_me
   return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
 }
 
+namespace swift {
+namespace {
+template <typename TIn, typename TOut>
+void launch_render(dim3 grid, cudaStream_t st, bool small, const TIn* src, const swift_image* im,
+                   const RenderRec* rec, const swift_mesh& mesh, TOut* out, int64_t out_pitch, int out_h, int out_w,
+                   float fill) {
+  if (small)
+    render_kernel<TIn, TOut, int><<<grid, 256, 0, st>>>(src, static_cast<int>(im->pitch), im->height, im->width, rec,
+                                                        mesh, out, static_cast<int>(out_pitch), out_h, out_w, fill);
+  else
+    render_kernel<TIn, TOut, long long><<<grid, 256, 0, st>>>(src, im->pitch, im->height, im->width, rec, mesh, out,
+                                                              out_pitch, out_h, out_w, fill);
+}
+}  // namespace
+}  // namespace swift
+
 extern "C" swift_status swift_render(const swift_image* src, swift_dtype dtype, const void* records,
-                                     const swift_mesh* mesh, float* out, int32_t out_h, int32_t out_w,
-                                     int64_t out_pitch, float fill, void* stream) {
+                                     const swift_mesh* mesh, void* out, swift_dtype out_dtype, int32_t out_h,
+                                     int32_t out_w, int64_t out_pitch, float fill, void* stream) {
   if (!src || !src->data || src->height < 2 || src->width < 2 || src->pitch < src->width) return SWIFT_ERR_INVALID_ARG;
   if (dtype != SWIFT_IN_U8 && dtype != SWIFT_IN_F32) return SWIFT_ERR_INVALID_ARG;
+  if (out_dtype != SWIFT_IN_U8 && out_dtype != SWIFT_IN_F32) return SWIFT_ERR_INVALID_ARG;
   if (!swift::mesh_ok(mesh) || !records || (reinterpret_cast<uintptr_t>(records) & 15) != 0 || !out || out_h < 0 ||
       out_w < 0 || out_pitch < out_w)
     return SWIFT_ERR_INVALID_ARG;
@@ -452,24 +477,20 @@ extern "C" swift_status swift_render(const swift_image* src, swift_dtype dtype, 
   const swift::RenderRec* rec = static_cast<const swift::RenderRec*>(records);
   const bool small = static_cast<long long>(src->height) * src->pitch < (1ll << 31) &&
                      static_cast<long long>(out_h) * out_pitch < (1ll << 31);
+  const uint8_t* s8 = static_cast<const uint8_t*>(src->data);
+  const float* sf = static_cast<const float*>(src->data);
+  float* of = static_cast<float*>(out);
+  uint8_t* o8 = static_cast<uint8_t*>(out);
   if (dtype == SWIFT_IN_U8) {
-    const uint8_t* s8 = static_cast<const uint8_t*>(src->data);
-    if (small)
-      swift::render_kernel<uint8_t, int><<<grid, 256, 0, st>>>(s8, static_cast<int>(src->pitch), src->height,
-                                                               src->width, rec, *mesh, out,
-                                                               static_cast<int>(out_pitch), out_h, out_w, fill);
+    if (out_dtype == SWIFT_IN_F32)
+      swift::launch_render(grid, st, small, s8, src, rec, *mesh, of, out_pitch, out_h, out_w, fill);
     else
-      swift::render_kernel<uint8_t, long long><<<grid, 256, 0, st>>>(s8, src->pitch, src->height, src->width, rec,
-                                                                     *mesh, out, out_pitch, out_h, out_w, fill);
+      swift::launch_render(grid, st, small, s8, src, rec, *mesh, o8, out_pitch, out_h, out_w, fill);
   } else {
-    const float* sf = static_cast<const float*>(src->data);
-    if (small)
-      swift::render_kernel<float, int><<<grid, 256, 0, st>>>(sf, static_cast<int>(src->pitch), src->height,
-                                                             src->width, rec, *mesh, out, static_cast<int>(out_pitch),
-                                                             out_h, out_w, fill);
+    if (out_dtype == SWIFT_IN_F32)
+      swift::launch_render(grid, st, small, sf, src, rec, *mesh, of, out_pitch, out_h, out_w, fill);
     else
-      swift::render_kernel<float, long long><<<grid, 256, 0, st>>>(sf, src->pitch, src->height, src->width, rec,
-                                                                   *mesh, out, out_pitch, out_h, out_w, fill);
+      swift::launch_render(grid, st, small, sf, src, rec, *mesh, o8, out_pitch, out_h, out_w, fill);
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
 }

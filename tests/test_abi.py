@@ -82,9 +82,10 @@ def test_mir_argument_errors_before_any_launch():
     assert lib.swift_render_prepare(dummy, C.byref(bad), dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_render_prepare(dummy, C.byref(good), C.c_void_p(8), None) == _lib.SWIFT_ERR_INVALID_ARG
     img = _lib.SwiftImage(None, 8, 0, 8, 8, 1)
-    assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 8, 8, 8, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 1, 8, 8, 8, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
     img = _lib.SwiftImage(16, 8, 0, 8, 8, 1)
-    assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 8, 8, 4, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 1, 8, 8, 4, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 7, 8, 8, 8, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_fit_affine(dummy, dummy, dummy, dummy, -1, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_fit_affine(None, None, None, None, 0, None, None, None) == _lib.SWIFT_OK
     assert lib.swift_correspondences(None, None, None, 4, 64, 0.0, None, None, None, None) == _lib.SWIFT_ERR_INVALID_ARG

@@ -102,3 +102,39 @@ def test_autotune_then_graph_replay(pyramid):
     for k in g2:
         assert (g2[k] == direct2[k]).all(), k
     assert not (g2["dx"] == g1["dx"]).all()
+
+
+def test_four_sizes_64_to_512_in_one_call_and_one_graph():
+    """Windows of 64, 128, 256 and 512 px mixed in one batch: one call, the
+    autotuner (512 streams only), one graph replay; oracle parity on a sample."""
+    a, b = synth.em_section_pair(1024, seed_content=57, seed_warp=58, seed_noise=(59, 60))
+    levels = [swift.Level(64, 0.5), swift.Level(128, 0.65), swift.Level(256, 0.8), swift.Level(512, 0.65, "hann", 1.0, 4.0)]
+    imgs_a = [synth.box_downsample(a, 4), synth.box_downsample(a, 2), a, a]
+    imgs_b = [synth.box_downsample(b, 4), synth.box_downsample(b, 2), b, b]
+    orgs, lvls = [], []
+    for k, (img, lv) in enumerate(zip(imgs_a, levels)):
+        o = synth.grid_origins(img.shape[0], lv.n, lv.n // 2)
+        orgs.append(o)
+        lvls.append(np.full(len(o), k, np.int32))
+    org = np.concatenate(orgs).astype(np.int32)
+    lvl = np.concatenate(lvls)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)  # noqa: E731
+    ta, tb, to, tl = [T(x) for x in imgs_a], [T(x) for x in imgs_b], T(org), T(lvl)
+    plan = swift.Plan(levels, dtype="u8", max_windows=len(org))
+    chosen, _ = plan.autotune(ta, tb, to, to, level=tl)
+    assert chosen[3] == "stream"
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        out = plan.capture(ta, tb, to, to, level=tl, stream=stream)
+        out.fill_(-1)
+        plan.replay(stream)
+    stream.synchronize()
+    g = swift.decode(out)
+    assert (g["status"] == 0).all()
+    rng = np.random.default_rng(61)
+    for l, lv in enumerate(levels):
+        idx = rng.choice(np.nonzero(lvl == l)[0], 2, replace=False)
+        olv = swim.Level(lv.n, lv.whiten_exponent, swim.APOD_HANN, 1.0, lv.snr_exclusion_radius)
+        for i in idx:
+            o, tied = oracle_window(swim.gather(imgs_b[l], org[i], lv.n), swim.gather(imgs_a[l], org[i], lv.n), olv)
+            compare(g, i, o, tied, lv.n, f"four sizes level {l}")
