@@ -20,6 +20,8 @@ Other workloads (``--workload``):
               moving section (metric: output pixels/s)
   remod       the model and pyramid steps: Z-averaged model of every section of a
               9-section 4096^2 stack and its 2x / 4x box-mean levels (metric: sections/s)
+  align       the registration loop: 8 sections of 1024^2 at known offsets, 3 iterations
+              of model / match / fit / render (metric: section-iterations/s)
 
 All inputs are seeded synthetic stand-ins for the paper's ssEM sections
 (``synth``).  Timing: W warm-up steps, then K timed steps; L2 is flushed (256 MiB
@@ -840,6 +842,91 @@ def remod_main(args, torch, swift, dev, world, rank):
         print(json.dumps(line))
 
 
+ALIGN_METRIC = "section-iterations/sec (registration loop: Z model, grid match, SNR-weighted affine, render)"
+
+
+def align_main(args, torch, swift, dev, world, rank):
+    """Workload: 8 crops (1024^2, uint8) of the headline EM-like section at
+    known offsets of up to +-6 px, independent noise; a step is one call of
+    the registration loop with 3 iterations (128^2 windows at stride 64, 225
+    per section, k = 3).  Timed by the host clock around each call (the loop
+    reads back one fit status and the window SNRs per section).  Metric:
+    section-iterations per second."""
+    import synth
+    from paper_1612_04787_gb300 import align
+    size, Z, n, stride, k, iters = 1024, 8, 128, 64, 3, 3
+    a, _ = synth.em_section_pair(2048)
+    rng = np.random.default_rng(95)
+    offs = rng.integers(-6, 7, (Z, 2))
+    raw = np.stack([np.clip(a[512 + dy:512 + dy + size, 512 + dx:512 + dx + size].astype(np.int16)
+                            + rng.integers(-6, 7, (size, size), dtype=np.int16), 0, 255).astype(np.uint8)
+                    for dy, dx in offs])
+    traw = torch.from_numpy(raw).to(dev)
+    lv = swift.Level(n, 0.65, "hann", 1.0, 3.0)
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        aligned, theta, hist = align.align_stack(traw, lv, stride, k, iters)
+    torch.cuda.synchronize(dev)
+    # displacement of the section centre (the translation at q = 0 trades off against A over 1024 px)
+    th = theta.cpu().numpy()
+    c = size / 2.0
+    disp = np.stack([th[:, 0] * c + th[:, 1] * c + th[:, 2] - c, th[:, 3] * c + th[:, 4] * c + th[:, 5] - c], 1)
+    resid = float(np.abs((disp - disp.mean(0)) + (offs - offs.mean(0))).max())
+    sampler = ClockSampler(local_rank())
+    sampler.start()
+    time.sleep(0.3)
+    steps = max(1, min(args.steps, 20))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        align.align_stack(traw, lv, stride, k, iters)
+    torch.cuda.synchronize(dev)
+    total_ms = (time.perf_counter() - t0) * 1e3
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    total_ms, value = aggregate_over_ranks(total_ms, Z * iters, steps, world, dev)
+    B = len(align.window_grid(size, size, n, stride))
+    match_flops = flops_per_pair(n) * B * Z * iters
+    achieved = match_flops / (total_ms / steps / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    print(f"[bench] align rank {rank}: {steps} steps, {total_ms / steps:.3f} ms/step, {value:.1f} "
+          f"section-iterations/s, offset residual {resid:.3f} px", file=sys.stderr, flush=True)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import driver as odrv, swim as osw
+        small = raw[:3, :256, :256]
+        t1 = time.perf_counter()
+        odrv.align_stack(small, osw.Level(64, 0.65, osw.APOD_HANN, 1.0, 3.0), 48, 2, 1)
+        dt = time.perf_counter() - t1
+        cpu = {"value": 3 / dt, "unit": "section-iterations/s", "cores": 1, "kind": "oracle",
+               "sample": f"one iteration on 3 sections of 256^2 with 64^2 windows (16 per section), FP64 oracle, "
+                         f"one process ({dt:.1f} s); a far smaller problem than the GPU step"}
+    line = {
+        "metric": ALIGN_METRIC, "value": value, "unit": "section-iterations/s", "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8 images, f32 match, f64 fits", "data": "synthetic",
+        "config": {"workload": f"{Z} sections of {size}x{size} uint8 at known offsets (+-6 px), {iters} iterations, "
+                               f"{B} windows of {n}^2 per section, k = {k}",
+                   "name": "align", "centre_offset_residual_px": resid, "median_snr_per_iteration": hist,
+                   "timing": "host clock around each call (the loop synchronises per section)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole loop (match flops only)",
+                     "peak_note": "derived FP32 FMA peak; achieved counts only the matches' algorithmic flops over "
+                                  "the whole loop's time"},
+        "e2e": {"value": value, "unit": "section-iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(Z * iters * (B * 32 + 4))},
+        "gpu_launches": steps * iters * (1 + 6 * Z),
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def local_rank() -> int:
     return int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -908,7 +995,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sections",
-                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "mir", "remod"])
+                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "mir", "remod",
+                             "align"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2", "fp16x2"])
     ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (sections workload)")
     ap.add_argument("--windows", type=int, default=0, help="limit the windows per step (small profiling cases)")
@@ -932,8 +1020,9 @@ def main():
     torch.cuda.set_device(dev)
     import paper_1612_04787_gb300 as swift
 
-    if args.workload in ("mir", "remod"):
-        (mir_main if args.workload == "mir" else remod_main)(args, torch, swift, dev, world, rank)
+    if args.workload in ("mir", "remod", "align"):
+        {"mir": mir_main, "remod": remod_main, "align": align_main}[args.workload](args, torch, swift, dev, world,
+                                                                                   rank)
         if world > 1:
             dist.destroy_process_group()
         return

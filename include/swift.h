@@ -371,15 +371,16 @@ swift_status swift_downsample(const swift_image* src, swift_dtype dtype, int32_t
                               void* stream);
 
 /* Z-averaged models of a uint8 section stack (device: section j at
- * stack + j * stride, rows `pitch` bytes apart): out[z] (float32, device, at
- * out + z * out_stride, rows out_pitch floats apart) is the mean of the
- * sections j in [z - k, z + k], j != z, with valid[j] != 0 (valid: device
- * uint8 [n_sections], NULL = all valid); with no such section it is section z
- * itself.  out = float32(integer sum) / float32(count), one IEEE division.
- * height <= 65535. */
+ * stack + j * stride, rows `pitch` bytes apart): model z (device, at
+ * out + z * out_stride elements, rows out_pitch elements apart) is the mean
+ * of the sections j in [z - k, z + k], j != z, with valid[j] != 0 (valid:
+ * device uint8 [n_sections], NULL = all valid); with no such section it is
+ * section z itself.  out_dtype SWIFT_IN_F32: float32(integer sum) /
+ * float32(count), one IEEE division; SWIFT_IN_U8: the exact mean rounded half
+ * to even.  height <= 65535. */
 swift_status swift_zmodel(const uint8_t* stack, int64_t stride, int32_t n_sections, int32_t height, int32_t width,
-                          int64_t pitch, int32_t k, const uint8_t* valid, float* out, int64_t out_stride,
-                          int64_t out_pitch, void* stream);
+                          int64_t pitch, int32_t k, const uint8_t* valid, void* out, swift_dtype out_dtype,
+                          int64_t out_stride, int64_t out_pitch, void* stream);
 
 /* Set the whitening exponent of one level for later calls (w in [0, 1]). */
 swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w);

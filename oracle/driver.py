@@ -12,8 +12,9 @@ suffices (Sec. IV).
 
 Readings where the paper is silent (also listed with the design notes):
 
-* one iteration: models of the current aligned stack (k neighbours each way,
-  the section itself excluded); every raw section is matched against its
+* one iteration: uint8 models of the current aligned stack (k neighbours
+  each way, the section itself excluded, the exact mean rounded half to
+  even); every raw section is matched against its
   model on a regular grid of windows (reference = model, moving = raw);
   the SNR-weighted least-squares affine maps the model frame to the raw
   section; the raw section is rendered through it (uint8, fill 0);
@@ -47,11 +48,10 @@ def align_stack(raw: np.ndarray, level: swim.Level, stride: int, k: int, iters: 
     mesh = mir.Mesh(0, 0, max(H, W), 1, 1)
     hist = []
     for _ in range(iters):
-        model = remod.zmodel(aligned, k)
+        model = remod.zmodel(aligned, k, dtype=np.uint8)
         snrs = []
         for z in range(Z):
-            res = [swim.match_pair(swim.gather(raw[z].astype(np.float32), o, n),
-                                   swim.gather(model[z], o, n), level) for o in org]
+            res = [swim.match_pair(swim.gather(raw[z], o, n), swim.gather(model[z], o, n), level) for o in org]
             q, p, w = mir.correspondences(res, org, org, n, min_snr)
             th, st = mir.fit_affine(q, p, w)
             if st == mir.OK:

@@ -24,8 +24,9 @@ Readings where the paper is silent (also listed with the design notes):
   block divided by f^2 in float32;
 * remod: the model of section z is the mean of the valid sections
   j in [z - k, z + k], j != z, clipped to the stack; float32 output is
-  float32(integer sum) / float32(count) (one correctly rounded division);
-  with no valid neighbour the model is the section itself.
+  float32(integer sum) / float32(count) (one correctly rounded division),
+  uint8 output the exact mean rounded half to even; with no valid neighbour
+  the model is the section itself.
 """
 from __future__ import annotations
 
@@ -55,16 +56,23 @@ def downsample(img: np.ndarray, f: int) -> np.ndarray:
     return (s / np.float32(f * f)).astype(np.float32)
 
 
-def zmodel(stack: np.ndarray, k: int, valid=None) -> np.ndarray:
-    """Model of every section of a uint8 [Z, H, W] stack: float32 [Z, H, W]."""
+def zmodel(stack: np.ndarray, k: int, valid=None, dtype=np.float32) -> np.ndarray:
+    """Model of every section of a uint8 [Z, H, W] stack: float32 [Z, H, W],
+    or uint8 (the exact mean rounded half to even) with dtype=np.uint8."""
     Z = stack.shape[0]
     valid = np.ones(Z, bool) if valid is None else np.asarray(valid, bool)
-    out = np.zeros(stack.shape, np.float32)
+    out = np.zeros(stack.shape, dtype)
     for z in range(Z):
         js = [j for j in range(max(0, z - k), min(Z, z + k + 1)) if j != z and valid[j]]
         if not js:
-            out[z] = stack[z].astype(np.float32)
+            out[z] = stack[z]
             continue
         s = sum(stack[j].astype(np.int64) for j in js)
-        out[z] = s.astype(np.float32) / np.float32(len(js))
+        if dtype == np.uint8:
+            c = len(js)
+            q, r = np.divmod(s, c)
+            q = q + ((2 * r > c) | ((2 * r == c) & (q % 2 == 1)))
+            out[z] = q.astype(np.uint8)
+        else:
+            out[z] = s.astype(np.float32) / np.float32(len(js))
     return out

@@ -408,16 +408,17 @@ def downsample(img, factor: int, out=None, stream=None):
     return out
 
 
-def zmodel(stack, k: int, valid=None, out=None, stream=None):
-    """Z-averaged models (float32 [Z, H, W]) of a uint8 [Z, H, W] CUDA stack:
-    the mean of the valid sections within +-k, the section itself excluded."""
+def zmodel(stack, k: int, valid=None, out=None, dtype=torch.float32, stream=None):
+    """Z-averaged models ([Z, H, W], float32 or uint8) of a uint8 [Z, H, W]
+    CUDA stack: the mean of the valid sections within +-k, the section itself
+    excluded (uint8: the exact mean rounded half to even)."""
     if stack.dtype != torch.uint8 or stack.dim() != 3 or not stack.is_cuda or stack.stride(2) != 1:
         raise TypeError("stack must be a [Z, H, W] uint8 CUDA tensor with contiguous rows")
     Z, H, W = stack.shape
     if out is None:
-        out = torch.empty((Z, H, W), dtype=torch.float32, device=stack.device)
-    elif out.dtype != torch.float32 or tuple(out.shape) != (Z, H, W) or out.stride(2) != 1:
-        raise ValueError("out must be a float32 [Z, H, W] tensor with contiguous rows")
+        out = torch.empty((Z, H, W), dtype=dtype, device=stack.device)
+    elif out.dtype not in (torch.float32, torch.uint8) or tuple(out.shape) != (Z, H, W) or out.stride(2) != 1:
+        raise ValueError("out must be a float32 or uint8 [Z, H, W] tensor with contiguous rows")
     vptr = None
     if valid is not None:
         valid = valid.to(device=stack.device, dtype=torch.uint8).contiguous()
@@ -425,5 +426,6 @@ def zmodel(stack, k: int, valid=None, out=None, stream=None):
             raise ValueError("valid must have one flag per section")
         vptr = valid.data_ptr()
     check(lib.swift_zmodel(stack.data_ptr(), stack.stride(0), Z, H, W, stack.stride(1), int(k), vptr,
-                           out.data_ptr(), out.stride(0), out.stride(1), _stream_ptr(stream)), "swift_zmodel")
+                           out.data_ptr(), DTYPE["u8" if out.dtype == torch.uint8 else "f32"], out.stride(0),
+                           out.stride(1), _stream_ptr(stream)), "swift_zmodel")
     return out

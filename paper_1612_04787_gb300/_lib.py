@@ -139,7 +139,7 @@ def _load():
     lib.swift_downsample.argtypes = [C.POINTER(SwiftImage), C.c_int, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]
     lib.swift_downsample.restype = C.c_int
     lib.swift_zmodel.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32,
-                                 C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
+                                 C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p]
     lib.swift_zmodel.restype = C.c_int
     return lib
 

@@ -86,15 +86,17 @@ __global__ void downsample_kernel(const T* src, long long pitch, long long strid
   }
 }
 
-// V pixels per thread (V = 4: 4-byte loads / 16-byte stores, rows aligned)
-template <int V>
+// V pixels per thread (V = 4: 4-byte loads / 16-byte (float) or 4-byte
+// (uint8) stores, rows aligned); TOut float: float32(sum) / float32(count),
+// uint8: the exact mean rounded half to even
+template <int V, typename TOut>
 __global__ void zmodel_kernel(const uint8_t* stack, long long stride, int Z, int H, int W, long long pitch, int k,
-                              const uint8_t* valid, float* out, long long out_stride, long long out_pitch) {
+                              const uint8_t* valid, TOut* out, long long out_stride, long long out_pitch) {
   const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   const int y = blockIdx.y;
   if (x0 >= W) return;
   const uint8_t* col = stack + static_cast<long long>(y) * pitch + x0;
-  float* ocol = out + static_cast<long long>(y) * out_pitch + x0;
+  TOut* ocol = out + static_cast<long long>(y) * out_pitch + x0;
   auto ok = [&](int j) { return valid == nullptr || __ldg(valid + j) != 0; };
   auto load = [&](int j, int (&v)[V]) {
     const uint8_t* p = col + static_cast<long long>(j) * stride;
@@ -138,17 +140,32 @@ __global__ void zmodel_kernel(const uint8_t* stack, long long stride, int Z, int
     load(z, c);
     const bool vz = ok(z);
     const int n = C - (vz ? 1 : 0);
-    float o[V];
+    TOut* op = ocol + static_cast<long long>(z) * out_stride;
+    if constexpr (sizeof(TOut) == 4) {
+      float o[V];
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-      const int s = S[i] - (vz ? c[i] : 0);
-      o[i] = n > 0 ? __fdiv_rn(static_cast<float>(s), static_cast<float>(n)) : static_cast<float>(c[i]);
-    }
-    float* op = ocol + static_cast<long long>(z) * out_stride;
-    if constexpr (V == 4) {
-      __stcs(reinterpret_cast<float4*>(op), make_float4(o[0], o[1], o[2], o[3]));
+      for (int i = 0; i < V; ++i) {
+        const int s = S[i] - (vz ? c[i] : 0);
+        o[i] = n > 0 ? __fdiv_rn(static_cast<float>(s), static_cast<float>(n)) : static_cast<float>(c[i]);
+      }
+      if constexpr (V == 4) {
+        __stcs(reinterpret_cast<float4*>(op), make_float4(o[0], o[1], o[2], o[3]));
+      } else {
+        __stcs(op, o[0]);
+      }
     } else {
-      __stcs(op, o[0]);
+      uint32_t o[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const int s = S[i] - (vz ? c[i] : 0);
+        o[i] = n > 0 ? round_half_even_div(static_cast<uint32_t>(s), static_cast<uint32_t>(n))
+                     : static_cast<uint32_t>(c[i]);
+      }
+      if constexpr (V == 4) {
+        *reinterpret_cast<uint32_t*>(op) = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
+      } else {
+        *op = static_cast<uint8_t>(o[0]);
+      }
     }
   }
 }
@@ -201,25 +218,37 @@ extern "C" swift_status swift_downsample(const swift_image* src, swift_dtype dty
 }
 
 extern "C" swift_status swift_zmodel(const uint8_t* stack, int64_t stride, int32_t n_sections, int32_t height,
-                                     int32_t width, int64_t pitch, int32_t k, const uint8_t* valid, float* out,
-                                     int64_t out_stride, int64_t out_pitch, void* stream) {
+                                     int32_t width, int64_t pitch, int32_t k, const uint8_t* valid, void* out,
+                                     swift_dtype out_dtype, int64_t out_stride, int64_t out_pitch, void* stream) {
   if (!stack || !out || n_sections < 0 || height < 0 || width < 0 || k < 0 || pitch < width || out_pitch < width)
     return SWIFT_ERR_INVALID_ARG;
+  if (out_dtype != SWIFT_IN_U8 && out_dtype != SWIFT_IN_F32) return SWIFT_ERR_INVALID_ARG;
   if (n_sections > 1 && (stride < pitch * height || out_stride < out_pitch * height)) return SWIFT_ERR_INVALID_ARG;
   if (n_sections == 0 || height == 0 || width == 0) return SWIFT_OK;
   if (height > 65535) return SWIFT_ERR_UNSUPPORTED;
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool f32 = out_dtype == SWIFT_IN_F32;
+  const int oalign = f32 ? 15 : 3;  // 16-byte float4 / 4-byte packed stores
   const bool vec = width % 4 == 0 && pitch % 4 == 0 && stride % 4 == 0 && out_pitch % 4 == 0 && out_stride % 4 == 0 &&
-                   (reinterpret_cast<uintptr_t>(stack) & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
-  if (vec) {
-    const dim3 grid((width / 4 + 127) / 128, height);
-    swift::zmodel_kernel<4><<<grid, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k, valid, out,
-                                                  out_stride, out_pitch);
+                   (reinterpret_cast<uintptr_t>(stack) & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & oalign) == 0;
+  const dim3 grid_v((width / 4 + 127) / 128, height), grid_s((width + 127) / 128, height);
+  if (f32) {
+    float* o = static_cast<float*>(out);
+    if (vec)
+      swift::zmodel_kernel<4, float><<<grid_v, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
+                                                             valid, o, out_stride, out_pitch);
+    else
+      swift::zmodel_kernel<1, float><<<grid_s, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
+                                                             valid, o, out_stride, out_pitch);
   } else {
-    const dim3 grid((width + 127) / 128, height);
-    swift::zmodel_kernel<1><<<grid, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k, valid, out,
-                                                  out_stride, out_pitch);
+    uint8_t* o = static_cast<uint8_t*>(out);
+    if (vec)
+      swift::zmodel_kernel<4, uint8_t><<<grid_v, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
+                                                               valid, o, out_stride, out_pitch);
+    else
+      swift::zmodel_kernel<1, uint8_t><<<grid_s, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
+                                                               valid, o, out_stride, out_pitch);
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
 }

@@ -58,3 +58,12 @@ def test_zmodel_excludes_damaged_sections_and_handles_isolation():
     np.testing.assert_allclose(iso[:, 0, 0], [10, 22.5, 35, 52.5, 70])
     out0 = remod.zmodel(stack, 0)  # k = 0: no neighbours, the section itself
     np.testing.assert_array_equal(out0, stack.astype(np.float32))
+
+
+def test_zmodel_uint8_rounds_the_exact_mean_half_to_even():
+    # neighbour sums over 2 sections: (1 + 2) / 2 = 1.5 -> 2, (2 + 3) / 2 = 2.5 -> 2, (4 + 5) / 2 = 4.5 -> 4
+    stack = np.stack([np.array([[1, 2, 4]], np.uint8), np.zeros((1, 3), np.uint8), np.array([[2, 3, 5]], np.uint8)])
+    out = remod.zmodel(stack, 1, dtype=np.uint8)
+    np.testing.assert_array_equal(out[1], [[2, 2, 4]])
+    np.testing.assert_array_equal(out[0], stack[1])  # single neighbour: exact
+    assert out.dtype == np.uint8

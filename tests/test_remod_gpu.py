@@ -69,3 +69,11 @@ def test_zmodel_feeds_the_match_as_a_reference():
     assert (r_model["status"] == 0).all()
     assert np.median(r_model["snr"]) > np.median(r_single["snr"])
     assert np.abs(r_model["sy"]).max() < 2.0 and np.abs(r_model["sx"]).max() < 2.0
+
+
+@pytest.mark.parametrize("width", [256, 257])
+def test_zmodel_uint8_bit_exact(width):
+    rng = np.random.default_rng(width)
+    stack = rng.integers(0, 256, (7, 33, width)).astype(np.uint8)
+    got = swift.zmodel(torch.from_numpy(stack).to(DEV), 3, dtype=torch.uint8).cpu().numpy()
+    np.testing.assert_array_equal(got, remod.zmodel(stack, 3, dtype=np.uint8))
