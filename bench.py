@@ -324,6 +324,39 @@ class Sections:
             ho.copy_(o, non_blocking=True)
         stream.synchronize()
 
+    def e2e_run(self, torch, stream, steps):
+        """Steps through the public API with host buffers, double-buffered: the
+        host-to-device copy of step k's sections (a copy stream) overlaps the
+        match of step k - 1; every step copies its inputs in and its results
+        out.  Returns the seconds from the first copy to the last result."""
+        if not hasattr(self, "d2"):
+            self.d2 = [(torch.empty_like(a), torch.empty_like(b)) for a, b in self.d]
+            self.org2 = torch.empty_like(self.dorg)
+            self.outs2 = [torch.empty_like(o) for o in self.outs]
+            self.copy_stream = torch.cuda.Stream(device=self.dorg.device)
+        sets = [(self.d, self.dorg, self.outs), (self.d2, self.org2, self.outs2)]
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            d, org, outs = sets[k % 2]
+            if k >= 2:
+                self.copy_stream.wait_event(done[k % 2])  # step k - 2 no longer reads these buffers
+            with torch.cuda.stream(self.copy_stream):
+                org.copy_(self.horg, non_blocking=True)
+                for (ha, hb), (da, db) in zip(self.h, d):
+                    da.copy_(ha, non_blocking=True)
+                    db.copy_(hb, non_blocking=True)
+                copied[k % 2].record(self.copy_stream)
+            stream.wait_event(copied[k % 2])
+            for (da, db), o, ho in zip(d, outs, self.hout):
+                self.plan.match(da, db, org, org, out=o, stream=stream)
+                ho.copy_(o, non_blocking=True)
+            done[k % 2].record(stream)
+        stream.synchronize()
+        return time.perf_counter() - t0
+
     def io_bytes(self):
         return sum(a.nbytes + b.nbytes for a, b in self.secs) + self.org.nbytes, self.windows * 32
 
@@ -1068,10 +1101,14 @@ def main():
     # e2e through the public API with host buffers
     e2e_steps = max(3, min(args.steps, 30))
     W.e2e_step(torch, stream)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        W.e2e_step(torch, stream)
-    e2e_s = time.perf_counter() - t0
+    if hasattr(W, "e2e_run"):
+        W.e2e_run(torch, stream, 2)
+        e2e_s = W.e2e_run(torch, stream, e2e_steps)
+    else:
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            W.e2e_step(torch, stream)
+        e2e_s = time.perf_counter() - t0
     e2e_value = world * W.windows * e2e_steps / e2e_s
     h2d, d2h = W.io_bytes()
 
@@ -1139,8 +1176,11 @@ def main():
                         "l2": "flushed before every timed step (256 MiB write, outside the step's events)",
                         "status_ok_fraction": ok_frac}, **W.config),
         "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": "windows/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": dict({"value": e2e_value, "unit": "windows/s", "h2d_bytes_per_step": int(h2d),
+                     "d2h_bytes_per_step": int(d2h)},
+                    **({"pipelining": "double-buffered: step k's host-to-device copy (copy stream) overlaps step "
+                                      "k-1's match; every step copies its sections in and its results out"}
+                       if hasattr(W, "e2e_run") else {})),
         "gpu_launches": args.steps * W.launches_per_step,
         "clocks": clocks,
     }
