@@ -85,7 +85,7 @@ namespace {
 constexpr long long kStreamSlice = SWIFT_STREAM_SLICE;
 // windows per slice of the affine / backward path
 constexpr long long kBackSlice = 1024;
-// default forward schedule: 256 x 256 and 128 x 128 windows stream their
+// default forward schedule: 128 x 128 and larger windows stream their
 // intermediates through the workspace; 64 x 64 windows use the fused kernel
 bool default_stream(int n) { return n >= 128; }
 }  // namespace
