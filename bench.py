@@ -1070,9 +1070,16 @@ def main():
 
     # per-kernel CUDA events around the library's launches (not under graph replay)
     timing = args.workload not in ("pyramid", "warp")
+    launches_per_step = {}
     if timing:
+        # one untimed step counts each kernel's launches per step; the timed
+        # region's event ring may keep only its most recent launches, so the
+        # windows per launch come from this count, not from the ring's size
         W.plan.set_timing(True)
         W.plan.timings()
+        W.step(stream)
+        torch.cuda.synchronize(dev)
+        launches_per_step = {k: v[1] for k, v in W.plan.timings().items()}
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -1140,7 +1147,7 @@ def main():
         dom = max(kt, key=lambda k: kt[k][0])
         launches = kt[dom][1]
         dom_ms = kt[dom][0] / launches
-        windows_per_launch = W.windows * args.steps / launches
+        windows_per_launch = W.windows / launches_per_step[dom]
         per_window = tensor_flops(W.dominant_n)[dom] if tensor else kernel_flops(W.dominant_n)[dom]
         achieved = per_window * windows_per_launch / (dom_ms / 1e3) / 1e12
         tot = sum(x[0] for x in kt.values())

@@ -263,8 +263,9 @@ swift_status swift_plan_replay(swift_plan plan, void* stream);
 /* Per-kernel timing.  While enabled, every forward launch records CUDA
  * events on its stream around each kernel (a ring of 1024 launch records);
  * swift_plan_timings synchronises on them and returns, per kernel slot, the
- * summed device time in ms and the number of launches since the last read,
- * then starts over.  Slots: 0 statistics, 1 row transforms, 2 column
+ * summed device time in ms and the number of launches since the last read
+ * (after more than 1024 launch records, the most recent 1024 only), then
+ * starts over.  Slots: 0 statistics, 1 row transforms, 2 column
  * transforms + whitening, 3 inverse row transforms, 4 finalize (the
  * streaming schedule, and the same five kernels of the BF16X2 / FP16X2
  * forms), 5 fused kernel, 6-7 unused.  kernel_ms and launches are host
