@@ -220,6 +220,23 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
+// Whitening factor |C|^-w from |C|^2 (Sec. II): 2^(-w/2 log2 |C|^2), 0 where
+// |C| = 0.  The base-2 logarithm and exponential are the hardware
+// approximations (PTX lg2.approx / ex2.approx, a few ulp); their
+// subnormal-flushing forms are safe because inputs below 2^-100 are first
+// scaled by 2^64 (exact) and the exponent stays within [-64, 75], so neither
+// instruction sees or makes a subnormal.
+__device__ __forceinline__ float whiten_factor(float mag2, float half_w) {
+  if (!(mag2 > 0.f)) return 0.f;
+  const bool tiny = mag2 < 0x1p-100f;
+  float lg, f;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(tiny ? mag2 * 0x1p64f : mag2));
+  if (tiny) lg -= 64.f;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(half_w * lg));
+  return f;
+}
+
+// ---------------------------------------------------------------------------
 // (value, index) ordering for the argmax: larger value wins, then smaller
 // index.  High 32 bits: order-preserving encoding of the float; low: ~index.
 __device__ __forceinline__ unsigned long long argmax_key(float v, uint32_t idx) {
@@ -673,7 +690,7 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
         const float2 c = make_float2(0.5f * fmaf(a.x, b.y, a.y * b.x),
                                      0.25f * ((a.x * a.x + a.y * a.y) - (b.x * b.x + b.y * b.y)));
         const float mag2 = fmaf(c.x, c.x, c.y * c.y);
-        const float s = mag2 > 0.f ? exp2f(half_w * log2f(mag2)) * inv_n2 : 0.f;
+        const float s = whiten_factor(mag2, half_w) * inv_n2;
         float2 g = make_float2(c.x * s, c.y * s);
         if (dc_col) {
           // the Nyquist column kx = n/2 rides along as the imaginary part: both
@@ -683,7 +700,7 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
           const float2 c2 = make_float2(0.5f * fmaf(a2.x, b2.y, a2.y * b2.x),
                                         0.25f * ((a2.x * a2.x + a2.y * a2.y) - (b2.x * b2.x + b2.y * b2.y)));
           const float mq = fmaf(c2.x, c2.x, c2.y * c2.y);
-          const float sq = mq > 0.f ? exp2f(half_w * log2f(mq)) * inv_n2 : 0.f;
+          const float sq = whiten_factor(mq, half_w) * inv_n2;
           if (ky == 0) g = make_float2(0.f, 0.f);  // G[0,0] = 0
           g = make_float2(g.x - c2.y * sq, g.y + c2.x * sq);
         }

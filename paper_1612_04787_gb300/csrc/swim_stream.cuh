@@ -42,6 +42,12 @@ struct StreamGeom {
   static constexpr int CB = N == 512 ? 8 : 16;  // K2: kx values (plus partners) per CTA
   static constexpr int NB2 = N / (2 * CB);
   static constexpr int T2 = 2 * CB * R2;   // K2: threads (one pass-A task each)
+  // K1 staging row stride (elements): the pad puts the rows that one warp's
+  // pass-A loads touch on different shared-memory banks
+  template <typename TIn>
+  static constexpr int stage_stride() {
+    return N + ((sizeof(TIn) == 4 && R2 == 8) ? 8 : 16);
+  }
   static constexpr int PB = (T / R2) < (N / 2) ? (T / R2) : (N / 2);  // K3: row pairs per CTA
   static constexpr int NB3 = (N / 2) / PB;
   static_assert(R1 * R2 == N, "radix");
@@ -126,38 +132,43 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
     constexpr int PER = N * N / VEC / 256;
     constexpr int BATCH = PER < 8 ? PER : 8;
     static_assert(PER % BATCH == 0, "vector batches");
+    // a thread's vectors all start at the same column x0 (256 is a multiple
+    // of the N / VEC vectors of a row): its VEC column tapers stay in registers
+    static_assert(256 % (N / VEC) == 0, "fixed column per thread");
+    const int x0 = (tid % (N / VEC)) * VEC;
+    float tx[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) tx[k] = tap[x0 + k];
 #pragma unroll 1
     for (int i0 = 0; i0 < PER; i0 += BATCH) {
       uint4 mqs[BATCH], rqs[BATCH];
 #pragma unroll
       for (int bq = 0; bq < BATCH; ++bq) {
-        const int e = tid + (i0 + bq) * 256;
-        const int y = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
+        const int y = (tid + (i0 + bq) * 256) / (N / VEC);
         mqs[bq] = __ldg(reinterpret_cast<const uint4*>(mbase + y * mpitch + x0));
         rqs[bq] = __ldg(reinterpret_cast<const uint4*>(rbase + y * rpitch + x0));
       }
 #pragma unroll
       for (int bq = 0; bq < BATCH; ++bq) {
-      const int e = tid + (i0 + bq) * 256;
-      const int y = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
-      const uint4 mq = mqs[bq], rq = rqs[bq];
-      const float ay = tap[y];
-      if constexpr (sizeof(TIn) == 1) {
-        const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w}, rw[4] = {rq.x, rq.y, rq.z, rq.w};
+        const int y = (tid + (i0 + bq) * 256) / (N / VEC);
+        const uint4 mq = mqs[bq], rq = rqs[bq];
+        const float ay = tap[y];
+        if constexpr (sizeof(TIn) == 1) {
+          const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w}, rw[4] = {rq.x, rq.y, rq.z, rq.w};
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float mv = static_cast<float>((mw[k >> 2] >> (8 * (k & 3))) & 0xffu);
-          const float rv = static_cast<float>((rw[k >> 2] >> (8 * (k & 3))) & 0xffu);
-          accum(ay * tap[x0 + k], mv, rv);
+          for (int k = 0; k < 16; ++k) {
+            const float mv = static_cast<float>((mw[k >> 2] >> (8 * (k & 3))) & 0xffu);
+            const float rv = static_cast<float>((rw[k >> 2] >> (8 * (k & 3))) & 0xffu);
+            accum(ay * tx[k], mv, rv);
+          }
+        } else {
+          const float mf[4] = {__uint_as_float(mq.x), __uint_as_float(mq.y), __uint_as_float(mq.z),
+                               __uint_as_float(mq.w)};
+          const float rf[4] = {__uint_as_float(rq.x), __uint_as_float(rq.y), __uint_as_float(rq.z),
+                               __uint_as_float(rq.w)};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) accum(ay * tx[k], mf[k], rf[k]);
         }
-      } else {
-        const float mf[4] = {__uint_as_float(mq.x), __uint_as_float(mq.y), __uint_as_float(mq.z),
-                             __uint_as_float(mq.w)};
-        const float rf[4] = {__uint_as_float(rq.x), __uint_as_float(rq.y), __uint_as_float(rq.z),
-                             __uint_as_float(rq.w)};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) accum(ay * tap[x0 + k], mf[k], rf[k]);
-      }
       }
     }
   } else {
@@ -211,6 +222,7 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, RB = G::RB, RS = G::RS, T = G::T;
   constexpr int KB = (RB * R1 + T - 1) / T;
+  constexpr int MS = G::template stage_stride<TIn>();
   const long long s = blockIdx.x / (N / RB);
   const int rb = blockIdx.x % (N / RB);
   const long long b = W.b0 + s;
@@ -223,8 +235,8 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   float* tap = reinterpret_cast<float*>(twid + N);
   // raw rows: uint8/float32 moving and reference; the reference of a K-section
   // model (or unaligned rows) is staged as float in rfstage, which aliases the slab
-  TIn* mstage = reinterpret_cast<TIn*>(tap + N);
-  TIn* rstage = mstage + RB * N;
+  TIn* mstage = reinterpret_cast<TIn*>(tap + N);  // [RB][MS]
+  TIn* rstage = mstage + RB * MS;
   float* rfstage = reinterpret_cast<float*>(slab);
   for (int i = tid; i < N; i += T) {
     twid[i] = L.twiddle[i];
@@ -268,21 +280,22 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
     for (int i = 0; i < (NV + T - 1) / T; ++i) {
       const int e = tid + i * T;
       if (NV % T == 0 || e < NV) {
-        reinterpret_cast<uint4*>(mstage)[e] = q[2 * i];
-        reinterpret_cast<uint4*>(rstage)[e] = q[2 * i + 1];
+        const int o = (e / (N / VEC)) * MS + (e % (N / VEC)) * VEC;
+        *reinterpret_cast<uint4*>(mstage + o) = q[2 * i];
+        *reinterpret_cast<uint4*>(rstage + o) = q[2 * i + 1];
       }
     }
   } else {
     const float inv_k = 1.0f / static_cast<float>(L.ref_count);
     for (int e = tid; e < RB * N; e += T) {
       const int r = e / N, x = e % N;
-      mstage[e] = static_cast<TIn>(load_px<TIn>(mbase + r * mpitch + x));
+      mstage[r * MS + x] = static_cast<TIn>(load_px<TIn>(mbase + r * mpitch + x));
       float rv = load_px<TIn>(rbase + r * rpitch + x);
       if (L.ref_count > 1) {
         for (int k = 1; k < L.ref_count; ++k) rv += load_px<TIn>(rbase + k * L.ref_stride + r * rpitch + x);
         rv *= inv_k;
       }
-      rfstage[e] = rv;
+      rfstage[r * MS + x] = rv;
     }
   }
   __syncthreads();
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   float mv[R1], rv[R1];
 #pragma unroll
   for (int m = 0; m < R1; ++m) {
-    const int e = line * N + j + R2 * m;
+    const int e = line * MS + j + R2 * m;
     mv[m] = static_cast<float>(mstage[e]);
     rv[m] = vec ? static_cast<float>(rstage[e]) : rfstage[e];
   }
@@ -408,7 +421,7 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
     const float2 c = make_float2(0.5f * fmaf(a.x, bb.y, a.y * bb.x),
                                  0.25f * ((a.x * a.x + a.y * a.y) - (bb.x * bb.x + bb.y * bb.y)));
     const float mag2 = fmaf(c.x, c.x, c.y * c.y);
-    const float sc = mag2 > 0.f ? exp2f(half_w * log2f(mag2)) * inv_n2 : 0.f;
+    const float sc = whiten_factor(mag2, half_w) * inv_n2;
     float2 g = make_float2(c.x * sc, c.y * sc);
     if constexpr (SAVE) {
       // R = (A - conj(B)) / 2i
@@ -427,7 +440,7 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
         cr[o + static_cast<size_t>(N) * (N / 2 + 1)] = make_float2(0.5f * (a2.y + b2.y), -0.5f * (a2.x - b2.x));
       }
       const float mq = fmaf(c2.x, c2.x, c2.y * c2.y);
-      const float sq = mq > 0.f ? exp2f(half_w * log2f(mq)) * inv_n2 : 0.f;
+      const float sq = whiten_factor(mq, half_w) * inv_n2;
       if (ky == 0) g = make_float2(0.f, 0.f);  // G[0,0] = 0
       g = make_float2(g.x - c2.y * sq, g.y + c2.x * sq);
     }
@@ -676,7 +689,8 @@ __global__ void __launch_bounds__(256) stream_final_kernel(const MatchLaunch L, 
 template <int N, typename TIn>
 constexpr size_t rows_smem() {
   using G = StreamGeom<N>;
-  return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * N + 2 * sizeof(TIn) * G::RB * N;
+  return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * N +
+         2 * sizeof(TIn) * G::RB * G::template stage_stride<TIn>();
 }
 template <int N>
 constexpr size_t cols_smem() {

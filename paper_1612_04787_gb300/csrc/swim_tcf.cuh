@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256, tcf_minb<N, false>()) tcf_cols_kernel(con
     const float2 c = make_float2(0.5f * fmaf(a.x, bb.y, a.y * bb.x),
                                  0.25f * ((a.x * a.x + a.y * a.y) - (bb.x * bb.x + bb.y * bb.y)));
     const float mag2 = fmaf(c.x, c.x, c.y * c.y);
-    float sc = mag2 > 0.f ? exp2f(half_w * log2f(mag2)) * inv_n2 : 0.f;
+    float sc = whiten_factor(mag2, half_w) * inv_n2;
     if (dc) sc = 0.f;  // G[0][0] = 0
     return make_float2(c.x * sc, c.y * sc);
   };
