@@ -783,7 +783,12 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
     // ---- inverse row pass B -> surface (kept in place), argmax ---------------
     // the surface stays in place (re: row y1, im: row y2 of each packed line);
     // the SNR pass below reads it back instead of holding it across barriers
-    unsigned long long best = 0ull;
+    // running maxima of the y1 rows and of the y2 rows: each thread meets
+    // either set in increasing row-major index, so a strict '>' keeps the
+    // smallest index among equal values (initial index: the thread's first
+    // pixel of each set); one argmax key per set at the end
+    float bva = -INFINITY, bvb = -INFINITY;
+    uint32_t bia = static_cast<uint32_t>((rank * ROWS + tid / R1) * N + tid % R1), bib = bia + HALF * N;
 #pragma unroll
     for (int i = 0; i < P::KBh; ++i) {
       const int task = tid + i * T;
@@ -803,12 +808,21 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
         for (int k2 = 0; k2 < R2; ++k2) {
           row[P::phys(R2 * k1 + k2)] = sv[k2];
           const int x = k1 + R1 * k2;
-          const unsigned long long ka = argmax_key(sv[k2].x, static_cast<uint32_t>(y1 * N + x));
-          const unsigned long long kb = argmax_key(sv[k2].y, static_cast<uint32_t>(y2 * N + x));
-          best = ka > best ? ka : best;
-          best = kb > best ? kb : best;
+          if (sv[k2].x > bva) {
+            bva = sv[k2].x;
+            bia = static_cast<uint32_t>(y1 * N + x);
+          }
+          if (sv[k2].y > bvb) {
+            bvb = sv[k2].y;
+            bib = static_cast<uint32_t>(y2 * N + x);
+          }
         }
       }
+    }
+    unsigned long long best = 0ull;
+    if ((P::TBh % T == 0) || tid < P::TBh) {  // threads without a task hold no pixel
+      const unsigned long long ka = argmax_key(bva, bia), kb = argmax_key(bvb, bib);
+      best = ka > kb ? ka : kb;
     }
     best = warp_max_u64(best);
     if (lane == 0) sc->wkey[warp] = best;

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
     const float inv_k = 1.0f / static_cast<float>(L.ref_count);
     for (int e = tid; e < RB * N; e += T) {
       const int r = e / N, x = e % N;
-      mstage[r * MS + x] = static_cast<TIn>(load_px<TIn>(mbase + r * mpitch + x));
+      mstage[r * MS + x] = __ldg(mbase + r * mpitch + x);
       float rv = load_px<TIn>(rbase + r * rpitch + x);
       if (L.ref_count > 1) {
         for (int k = 1; k < L.ref_count; ++k) rv += load_px<TIn>(rbase + k * L.ref_stride + r * rpitch + x);
@@ -548,7 +548,12 @@ __global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, 
   }
   __syncthreads();
   float* surf = reinterpret_cast<float*>(W.zr + s * N * N);  // [N][N] response
-  unsigned long long best = 0ull;
+  // running maxima of the y1 rows and of the y2 rows: each thread meets either
+  // set in increasing row-major index, so a strict '>' keeps the smallest
+  // index among equal values; one argmax key per set at the end
+  // (initial index: the thread's first pixel of each set)
+  float bva = -INFINITY, bvb = -INFINITY;
+  uint32_t bia = static_cast<uint32_t>((pb * PB + tid / R1) * N + tid % R1), bib = bia + (N / 2) * N;
   float s1 = 0.f, s2 = 0.f;  // sums of s and s^2 over every pixel of the block
 #pragma unroll
   for (int i = 0; i < (TB + T - 1) / T; ++i) {
@@ -571,11 +576,20 @@ __global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, 
       surf[y2 * N + x] = v[k2].y;
       s1 += v[k2].x + v[k2].y;
       s2 = fmaf(v[k2].x, v[k2].x, fmaf(v[k2].y, v[k2].y, s2));
-      const unsigned long long ka = argmax_key(v[k2].x, static_cast<uint32_t>(y1 * N + x));
-      const unsigned long long kb = argmax_key(v[k2].y, static_cast<uint32_t>(y2 * N + x));
-      best = ka > best ? ka : best;
-      best = kb > best ? kb : best;
+      if (v[k2].x > bva) {
+        bva = v[k2].x;
+        bia = static_cast<uint32_t>(y1 * N + x);
+      }
+      if (v[k2].y > bvb) {
+        bvb = v[k2].y;
+        bib = static_cast<uint32_t>(y2 * N + x);
+      }
     }
+  }
+  unsigned long long best = 0ull;
+  if (TB % T == 0 || tid < TB) {  // n = 512: threads without a task hold no pixel
+    const unsigned long long ka = argmax_key(bva, bia), kb = argmax_key(bvb, bib);
+    best = ka > kb ? ka : kb;
   }
   best = warp_max_u64(best);
   const double d1 = warp_sum_f64(static_cast<double>(s1)), d2 = warp_sum_f64(static_cast<double>(s2));

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256, tcf_minb<N, true>()) tcf_rows_kernel(cons
     const float inv_k = 1.0f / static_cast<float>(L.ref_count);
     for (int e = tid; e < RT * N; e += 256) {
       const int r = e / N, x = e % N;
-      mstage[r * N + tcf_stage_pos<TIn>(x)] = static_cast<TIn>(load_px<TIn>(mbase + r * mpitch + x));
+      mstage[r * N + tcf_stage_pos<TIn>(x)] = __ldg(mbase + r * mpitch + x);
       float rv = load_px<TIn>(rbase + r * rpitch + x);
       if (L.ref_count > 1) {
         for (int k = 1; k < L.ref_count; ++k) rv += load_px<TIn>(rbase + k * L.ref_stride + r * rpitch + x);
