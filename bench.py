@@ -220,19 +220,21 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # ncu-derived traffic for the dominant kernel (valid only for unchanged sources)
 # --------------------------------------------------------------------------- #
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=None) -> str:
+    """SHA-256 (16 hex digits) over the given csrc files (all .cu / .cuh / .h
+    files when None), in sorted order."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1612_04787_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    names = files if files is not None else [f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h"))]
+    for f in sorted(names):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel_key: str, windows_per_launch: int):
     """DRAM bytes per launch from a committed ncu capture, scaled to this
-    launch's windows (traffic grows in proportion), or None when the kernel
-    sources changed since the capture."""
+    launch's windows (traffic grows in proportion), or None when a source file
+    of that kernel (the record's "sources") changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -240,7 +242,7 @@ def recorded_traffic(kernel_key: str, windows_per_launch: int):
         rec = json.load(open(path)).get(kernel_key)
     except (ValueError, OSError):
         return None
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(rec.get("sources")):
         return None
     return rec["dram_bytes_per_window"] * windows_per_launch
 

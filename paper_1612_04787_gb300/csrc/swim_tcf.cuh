@@ -168,28 +168,36 @@ struct WarpDft {
       }
     }
     // first product: D1[(mt, k1)][n2] = sum_(ks, n1) F16big[(mt, k1)][(ks, n1)] x[(ks, n1)][n2]
-    float d1[2][G::NT1][4];
+    // (the data operand is split once per (j, ks); each constant fragment is
+    // read from shared memory once per transform)
+    uint32_t bsp[G::NT1][2][4];  // hi0, hi1, lo0, lo1
 #pragma unroll
-    for (int j = 0; j < G::NT1; ++j) {
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) d1[mt][j][0] = d1[mt][j][1] = d1[mt][j][2] = d1[mt][j][3] = 0.f;
+    for (int j = 0; j < G::NT1; ++j)
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
         float v[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] = (ks == 0 ? x[c + 4 * j].x : cj * x[c + 4 * j].y) * sc;
-        uint32_t bh0, bl0, bh1, bl1;
-        tcf_split<FP16>(v[0], v[1], bh0, bl0);
-        tcf_split<FP16>(v[2], v[3], bh1, bl1);
+        tcf_split<FP16>(v[0], v[1], bsp[j][ks][0], bsp[j][ks][2]);
+        tcf_split<FP16>(v[2], v[3], bsp[j][ks][1], bsp[j][ks][3]);
+      }
+    float d1[2][G::NT1][4];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          const uint4 ah = frag(2 * mt + ks), al = frag(4 + 2 * mt + ks);
-          tcf_mma<FP16>(d1[mt][j], al.x, al.y, al.z, al.w, bh0, bh1);
-          tcf_mma<FP16>(d1[mt][j], ah.x, ah.y, ah.z, ah.w, bl0, bl1);
-          tcf_mma<FP16>(d1[mt][j], ah.x, ah.y, ah.z, ah.w, bh0, bh1);
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int j = 0; j < G::NT1; ++j) d1[mt][j][0] = d1[mt][j][1] = d1[mt][j][2] = d1[mt][j][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const uint4 ah = frag(2 * mt + ks), al = frag(4 + 2 * mt + ks);
+#pragma unroll
+        for (int j = 0; j < G::NT1; ++j) {
+          tcf_mma<FP16>(d1[mt][j], al.x, al.y, al.z, al.w, bsp[j][ks][0], bsp[j][ks][1]);
+          tcf_mma<FP16>(d1[mt][j], ah.x, ah.y, ah.z, ah.w, bsp[j][ks][2], bsp[j][ks][3]);
+          tcf_mma<FP16>(d1[mt][j], ah.x, ah.y, ah.z, ah.w, bsp[j][ks][0], bsp[j][ks][1]);
         }
       }
-    }
     // twiddles (and the FP16 stage scale)
     constexpr float s16 = FP16 ? 0.0625f : 1.0f;
     const int g = lane >> 2, t = lane & 3;
@@ -221,17 +229,25 @@ struct WarpDft {
         tcf_split<FP16>(d1[1][0][0], d1[1][0][1], ah[2], al[2]);
         tcf_split<FP16>(d1[1][0][2], d1[1][0][3], ah[3], al[3]);
       }
+      // B fragments: F16big^T (Q = 16; fragment (ks, n = 2 mt + h) = A fragment
+      // (mt, ks) registers h, 2 + h) or F8big; each read once per k-step
+      uint4 fh[(G::NT3 + 1) / 2], fl[(G::NT3 + 1) / 2];
+#pragma unroll
+      for (int p = 0; p < (G::NT3 + 1) / 2; ++p) {
+        fh[p] = G::Q == 16 ? frag(2 * p + ks) : frag(8);
+        fl[p] = G::Q == 16 ? frag(4 + 2 * p + ks) : frag(9);
+      }
 #pragma unroll
       for (int n = 0; n < G::NT3; ++n) {
         uint32_t bh0, bh1, bl0, bl1;
-        if constexpr (G::Q == 16) {  // F16big^T: B fragment (ks, n = 2 mt + h) = A fragment (mt, ks) regs h, 2 + h
-          const uint4 fh = frag(2 * (n >> 1) + ks), fl = frag(4 + 2 * (n >> 1) + ks);
-          bh0 = (n & 1) ? fh.y : fh.x;
-          bh1 = (n & 1) ? fh.w : fh.z;
-          bl0 = (n & 1) ? fl.y : fl.x;
-          bl1 = (n & 1) ? fl.w : fl.z;
+        if constexpr (G::Q == 16) {
+          const uint4 h4 = fh[n >> 1], l4 = fl[n >> 1];
+          bh0 = (n & 1) ? h4.y : h4.x;
+          bh1 = (n & 1) ? h4.w : h4.z;
+          bl0 = (n & 1) ? l4.y : l4.x;
+          bl1 = (n & 1) ? l4.w : l4.z;
         } else {
-          const uint4 gh = frag(8), gl = frag(9);
+          const uint4 gh = fh[0], gl = fl[0];
           bh0 = n ? gh.z : gh.x;
           bh1 = n ? gh.w : gh.y;
           bl0 = n ? gl.z : gl.x;
