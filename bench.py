@@ -885,8 +885,8 @@ def align_main(args, torch, swift, dev, world, rank):
     known offsets of up to +-6 px, independent noise; a step is one call of
     the registration loop with 3 iterations (128^2 windows at stride 64, 225
     per section, k = 3).  Timed by the host clock around each call (the loop
-    reads back one fit status and the window SNRs per section).  Metric:
-    section-iterations per second."""
+    reads back the fit statuses and the window results once per iteration).
+    Metric: section-iterations per second."""
     import synth
     from paper_1612_04787_gb300 import align
     size, Z, n, stride, k, iters = 1024, 8, 128, 64, 3, 3
@@ -946,14 +946,14 @@ def align_main(args, torch, swift, dev, world, rank):
         "config": {"workload": f"{Z} sections of {size}x{size} uint8 at known offsets (+-6 px), {iters} iterations, "
                                f"{B} windows of {n}^2 per section, k = {k}",
                    "name": "align", "centre_offset_residual_px": resid, "median_snr_per_iteration": hist,
-                   "timing": "host clock around each call (the loop synchronises per section)"},
+                   "timing": "host clock around each call (the loop synchronises once per iteration)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "whole loop (match flops only)",
                      "peak_note": "derived FP32 FMA peak; achieved counts only the matches' algorithmic flops over "
                                   "the whole loop's time"},
         "e2e": {"value": value, "unit": "section-iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(Z * iters * (B * 32 + 4))},
-        "gpu_launches": steps * iters * (1 + 6 * Z),
+        "gpu_launches": steps * iters * (3 + 7 * Z),  # per iteration: models, 5 per match, correspondences, fit, 2 per render
         "clocks": clocks,
     }
     if cpu is not None:

@@ -38,7 +38,14 @@ def align_stack(raw: torch.Tensor, level: Level, stride: int, k: int, iters: int
                 min_snr: float = 0.0, stream=None):
     """Align a uint8 [Z, H, W] CUDA stack.  Returns (aligned uint8 [Z, H, W],
     theta float64 [Z, 6] (model frame -> raw section: p = A q + t), list of
-    the median SNR of every iteration)."""
+    the median SNR of every iteration).
+
+    Per iteration: the Z models, then every section's grid match (one call per
+    section), then one correspondence call and one grouped fit over all
+    sections, one read-back of the fit statuses and the match results, and
+    the renders.  A section's match and fit depend only on the models built at
+    the start of the iteration, so queueing them all before the read-back
+    gives the same affines as handling the sections one by one."""
     if raw.dtype != torch.uint8 or raw.dim() != 3 or not raw.is_cuda or not raw.is_contiguous():
         raise TypeError("raw must be a contiguous uint8 [Z, H, W] CUDA tensor")
     Z, H, W = raw.shape
@@ -46,30 +53,34 @@ def align_stack(raw: torch.Tensor, level: Level, stride: int, k: int, iters: int
     n = level.n
     org = torch.from_numpy(window_grid(H, W, n, stride)).to(dev)
     B = int(org.shape[0])
+    org_all = org.repeat(Z, 1)  # the same grid in every section
+    offsets = torch.arange(0, (Z + 1) * B, B, dtype=torch.int64, device=dev)
     plan = Plan([level], dtype="u8", max_windows=B)
     aligned = raw.clone()
     model = torch.empty_like(raw)
     theta = torch.tensor([1.0, 0.0, 0.0, 0.0, 1.0, 0.0], dtype=torch.float64, device=dev).repeat(Z, 1)
     mesh = Mesh(0, 0, max(H, W), 1, 1)
     recs = torch.empty((mesh.n_triangles, 8), dtype=torch.float32, device=dev)
-    res = torch.empty((B, 8), dtype=torch.int32, device=dev)
+    res = torch.empty((Z, B, 8), dtype=torch.int32, device=dev)
     hist = []
     for _ in range(iters):
         zmodel(aligned, k, out=model, stream=stream)
-        snrs = []
         for z in range(Z):
-            plan.match(model[z], raw[z], org, org, out=res, stream=stream)
-            q, p, w = correspondences(res, org, org, n, min_snr, stream=stream)
-            th, st = fit_affine(q, p, w, stream=stream)
-            if int(st[0]) == FIT_OK:
-                theta[z] = th[0]
+            plan.match(model[z], raw[z], org, org, out=res[z], stream=stream)
+        q, p, w = correspondences(res.view(Z * B, 8), org_all, org_all, n, min_snr, stream=stream)
+        th, st = fit_affine(q, p, w, offsets=offsets, stream=stream)
+        if stream is not None:
+            stream.synchronize()
+        ok = st.cpu().numpy() == FIT_OK  # a degenerate fit keeps the section's previous affine
+        d = decode(res.view(Z * B, 8))
+        for z in range(Z):
+            if ok[z]:
+                theta[z] = th[z]
             tri = theta[z].repeat(mesh.n_triangles, 1)
             render_records(tri, mesh, records=recs, stream=stream)
             render(raw[z], tri, mesh, H, W, fill=0.0, out=aligned[z], records=recs, stream=stream)
-            d = decode(res)
-            ok = (d["status"] == 0) & np.isfinite(d["snr"])
-            snrs.extend(d["snr"][ok].tolist())
-        hist.append(float(np.median(snrs)) if snrs else 0.0)
+        good = (d["status"] == 0) & np.isfinite(d["snr"])
+        hist.append(float(np.median(d["snr"][good])) if good.any() else 0.0)
         if len(hist) > 1 and abs(hist[-1] - hist[-2]) <= tol * abs(hist[-2]):
             break
     return aligned, theta, hist
