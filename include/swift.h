@@ -271,6 +271,17 @@ swift_status swift_plan_replay(swift_plan plan, void* stream);
  * forms), 5 fused kernel, 6-7 unused.  kernel_ms and launches are host
  * arrays of 8. */
 swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
+
+/* Test hook for the bounded-wait failure path (not for production use).
+ * While enabled, the FP32 streaming schedule's staging of aligned float32
+ * rows (bulk asynchronous copies counted on an mbarrier) expects 16 bytes
+ * more than its copies deliver, so its wait gives up after its bound (about
+ * 2 s, then about 2 s more for copies in flight) and every such window
+ * reports SWIFT_WIN_TIMEOUT.  Nothing faults or hangs; the stream and the
+ * plan stay usable, and calls after disabling it give normal results.
+ * uint8 windows, the fused schedule and the tensor-core forms do not use
+ * this staging and are unaffected. */
+swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enable);
 swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, int32_t* launches);
 
 /* ------------------------------------------------------------------------

@@ -171,6 +171,11 @@ class Plan:
 
     KERNEL_SLOTS = ("stats", "rows", "cols", "irows", "final", "fused")
 
+    def set_test_stall(self, enable: bool):
+        """Test hook: float32 row staging waits for bytes that never arrive,
+        so its bounded wait runs out and windows report status 4 (timeout)."""
+        check(lib.swift_plan_set_test_stall(self._h, 1 if enable else 0), "swift_plan_set_test_stall")
+
     def set_timing(self, enable: bool):
         """Record CUDA events around every kernel of later forward calls."""
         check(lib.swift_plan_set_timing(self._h, 1 if enable else 0), "swift_plan_set_timing")

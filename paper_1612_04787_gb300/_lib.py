@@ -40,6 +40,7 @@ EXPORTS = (
     "swift_plan_capture",
     "swift_plan_replay",
     "swift_plan_set_timing",
+    "swift_plan_set_test_stall",
     "swift_plan_timings",
     "swift_status_string",
     "swift_version",
@@ -116,6 +117,8 @@ def _load():
     lib.swift_plan_replay.restype = C.c_int
     lib.swift_plan_set_timing.argtypes = [C.c_void_p, C.c_int32]
     lib.swift_plan_set_timing.restype = C.c_int
+    lib.swift_plan_set_test_stall.argtypes = [C.c_void_p, C.c_int32]
+    lib.swift_plan_set_test_stall.restype = C.c_int
     lib.swift_plan_timings.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
     lib.swift_plan_timings.restype = C.c_int
     lib.swift_status_string.argtypes = [C.c_int]

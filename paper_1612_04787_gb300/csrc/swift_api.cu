@@ -68,6 +68,7 @@ struct swift_plan_s {
   double* gw_acc = nullptr;  // [kMaxLevels] accumulated dL/dw
   // per-kernel timing (swift_plan_set_timing / swift_plan_timings): a ring
   // of event sets, one set per streaming slice or fused launch
+  bool test_stall = false;  // swift_plan_set_test_stall
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // [kTimingSets][6]
   int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch
@@ -254,6 +255,7 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
   L.inv_sum_a = plan->inv_sum_a[l];
   L.taper = plan->taper[l];
   L.twiddle = plan->twiddle[size_slot(lv.n)];
+  L.stall_tx = plan->test_stall ? 16u : 0u;
   L.out = out;
   if (plan->prec != SWIFT_PREC_FP32) {
     const bool fp16 = plan->prec == SWIFT_PREC_FP16X2;
@@ -362,6 +364,7 @@ static swift::MatchLaunch level_launch(swift_plan plan, const swift_batch* batch
   L.inv_sum_a = plan->inv_sum_a[l];
   L.taper = plan->taper[l];
   L.twiddle = plan->twiddle[size_slot(lv.n)];
+  L.stall_tx = plan->test_stall ? 16u : 0u;
   L.out = out;
   L.pre_status = nullptr;
   return L;
@@ -557,6 +560,12 @@ extern "C" swift_status swift_plan_replay(swift_plan plan, void* stream) {
     cudaGetLastError();
     return SWIFT_ERR_CUDA;
   }
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enable) {
+  if (!plan) return SWIFT_ERR_INVALID_ARG;
+  plan->test_stall = enable != 0;
   return SWIFT_OK;
 }
 

@@ -28,6 +28,7 @@ struct MatchLaunch {
   const float2* twiddle;             // [R2][R1] forward W_n^{j m}
   swift_result* out;                 // [B]
   const int* pre_status = nullptr;   // [slice] status decided before the statistics (or null)
+  unsigned int stall_tx = 0;         // test hook: bytes the float row staging waits for that never arrive
 };
 
 // Workspace of the streaming forward path for one slice of windows.

@@ -259,30 +259,62 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   }
   mbase += static_cast<long long>(rb * RB) * mpitch;
   rbase += static_cast<long long>(rb * RB) * rpitch;
-  // stage the block's RB rows of both windows: 16-byte vector loads when aligned
-  constexpr int VEC = 16 / static_cast<int>(sizeof(TIn));
-  constexpr int NV = RB * N / VEC;  // vectors per image
+  // stage the block's RB rows of both windows when they are 16-byte aligned:
+  // uint8 rows (256 B at n = 256) by 16-byte vector loads; float rows (1 KB)
+  // by bulk asynchronous copies (cp.async.bulk issued by one thread,
+  // completion counted on an mbarrier), which measured faster for them and
+  // slower for the short uint8 rows.  The copy wait is bounded (about 2 s): a
+  // block whose copies did not arrive marks its window SWIFT_WIN_TIMEOUT,
+  // waits once more for the copies in flight and leaves.
   const bool vec = L.ref_count == 1 && ((reinterpret_cast<uintptr_t>(mbase) | reinterpret_cast<uintptr_t>(rbase) |
                                          static_cast<uintptr_t>(mpitch * sizeof(TIn)) |
                                          static_cast<uintptr_t>(rpitch * sizeof(TIn))) & 15) == 0;
   if (vec) {
-    uint4 q[2 * ((NV + T - 1) / T)];
-#pragma unroll
-    for (int i = 0; i < (NV + T - 1) / T; ++i) {
-      const int e = tid + i * T;
-      if (NV % T == 0 || e < NV) {
-        const int r = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
-        q[2 * i] = __ldg(reinterpret_cast<const uint4*>(mbase + r * mpitch + x0));
-        q[2 * i + 1] = __ldg(reinterpret_cast<const uint4*>(rbase + r * rpitch + x0));
+    if constexpr (sizeof(TIn) == 4) {
+      __shared__ __align__(8) unsigned long long stage_bar;
+      const uint32_t mbar = smem_addr(&stage_bar);
+      constexpr uint32_t kRowBytes = N * sizeof(TIn);
+      static_assert(kRowBytes % 16 == 0 && (MS * sizeof(TIn)) % 16 == 0, "bulk copy granularity");
+      if (tid == 0) {
+        mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(mbar, 2 * RB * kRowBytes + L.stall_tx);
+        for (int r = 0; r < RB; ++r) {
+          bulk_g2s(smem_addr(mstage + r * MS), mbase + r * mpitch, kRowBytes, mbar);
+          bulk_g2s(smem_addr(rstage + r * MS), rbase + r * rpitch, kRowBytes, mbar);
+        }
       }
-    }
+      __syncthreads();  // the barrier is initialised before anyone waits on it
+      const bool arrived = mbar_wait_bounded(mbar, 0);
+      if (__syncthreads_or(!arrived)) {
+        if (tid == 0) {
+          mbar_wait_bounded(mbar, 0);
+          W.stats[s] = make_float4(0.f, 0.f, __int_as_float(SWIFT_WIN_TIMEOUT), 0.f);
+        }
+        return;
+      }
+    } else {
+      constexpr int VEC = 16 / static_cast<int>(sizeof(TIn));
+      constexpr int NV = RB * N / VEC;  // vectors per image
+      uint4 q[2 * ((NV + T - 1) / T)];
 #pragma unroll
-    for (int i = 0; i < (NV + T - 1) / T; ++i) {
-      const int e = tid + i * T;
-      if (NV % T == 0 || e < NV) {
-        const int o = (e / (N / VEC)) * MS + (e % (N / VEC)) * VEC;
-        *reinterpret_cast<uint4*>(mstage + o) = q[2 * i];
-        *reinterpret_cast<uint4*>(rstage + o) = q[2 * i + 1];
+      for (int i = 0; i < (NV + T - 1) / T; ++i) {
+        const int e = tid + i * T;
+        if (NV % T == 0 || e < NV) {
+          const int r = e / (N / VEC), x0 = (e % (N / VEC)) * VEC;
+          q[2 * i] = __ldg(reinterpret_cast<const uint4*>(mbase + r * mpitch + x0));
+          q[2 * i + 1] = __ldg(reinterpret_cast<const uint4*>(rbase + r * rpitch + x0));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < (NV + T - 1) / T; ++i) {
+        const int e = tid + i * T;
+        if (NV % T == 0 || e < NV) {
+          const int o = (e / (N / VEC)) * MS + (e % (N / VEC)) * VEC;
+          *reinterpret_cast<uint4*>(mstage + o) = q[2 * i];
+          *reinterpret_cast<uint4*>(rstage + o) = q[2 * i + 1];
+        }
       }
     }
   } else {

@@ -127,6 +127,29 @@ def test_shifted_patches_f32(sections, n):
         assert abs(g["sy"][i] - d[i, 0]) < 1.0 and abs(g["sx"][i] - d[i, 1]) < 1.0
 
 
+def test_staging_wait_runs_out_and_is_reported(sections):
+    """The bounded wait of the float row staging, made to run out on purpose:
+    with the test hook on, the copies expect 16 bytes that never arrive, the
+    wait gives up after its bound and every window reports SWIFT_WIN_TIMEOUT
+    (4); nothing faults, and the same plan then gives normal results (the
+    context stays usable)."""
+    a, _ = sections
+    n = 128
+    ref, mov, _ = synth.shifted_patches(a, n, 4, seed=77)
+    lv = swift.Level(n, 0.65, "hann", 1.0, 3.0)
+    plan = swift.Plan([lv], dtype="f32", max_windows=4)
+    tr, tm = torch.from_numpy(ref).to(DEV), torch.from_numpy(mov).to(DEV)
+    base = swift.decode(plan.match(tr, tm))
+    assert (base["status"] == 0).all()
+    plan.set_test_stall(True)
+    stalled = swift.decode(plan.match(tr, tm))
+    plan.set_test_stall(False)
+    assert (stalled["status"] == 4).all(), stalled["status"]
+    again = swift.decode(plan.match(tr, tm))
+    for k in base:
+        assert (again[k] == base[k]).all(), k
+
+
 def test_projection_reference(sections):
     a, b = sections
     n = 128
