@@ -150,6 +150,26 @@ def test_staging_wait_runs_out_and_is_reported(sections):
         assert (again[k] == base[k]).all(), k
 
 
+@pytest.mark.parametrize("n", [128, 256])
+def test_float_sections_aligned_and_unaligned_origins(sections, n):
+    """float32 sections in section mode: windows whose rows start on 16-byte
+    boundaries are staged by bulk asynchronous copies, the others by scalar
+    loads; both kinds mixed in one call match the oracle."""
+    a, b = sections
+    fa = (a.astype(np.float32) * 0.5 - 3.0)
+    fb = (b.astype(np.float32) * 0.5 - 3.0)
+    rng = np.random.default_rng(n + 3)
+    ro = synth.random_origins(8, 1024, 1024, n, seed=n + 4, margin=2)
+    ro[::2] -= ro[::2] % 4  # x multiple of 4 floats: 16-byte aligned rows (pitch 1024 floats)
+    mo = np.clip(ro + rng.integers(-4, 5, ro.shape), 0, 1024 - n).astype(np.int32)
+    mo[0:4:2] = np.clip(ro[0:4:2] + np.array([[4, -8], [-4, 4]]), 0, 1024 - n)  # both rows aligned
+    assert (ro[0:4:2, 1] % 4 == 0).all() and (mo[0:4:2, 1] % 4 == 0).all() and (mo[1::2, 1] % 4 != 0).any()
+    lv = swift.Level(n, 0.65, "hann", 1.0, 3.0)
+    g = run_sections(fa, fb, ro, mo, lv, dtype="f32")
+    assert (g["status"] == 0).all()
+    check_sections(fa.astype(np.float64), fb.astype(np.float64), ro, mo, lv, g, f"float sections n={n}")
+
+
 def test_projection_reference(sections):
     a, b = sections
     n = 128
