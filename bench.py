@@ -753,7 +753,7 @@ def mir_main(args, torch, swift, dev, world, rank):
                    "name": "mir", "fit_ok_fraction": ok_frac, "fit_ms": fit_ms, "render_ms": render_ms,
                    "l2": "flushed before every timed step (256 MiB write, outside the step's events)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "render_kernel<u8>",
+                     "traffic": None, "kernel": "render_run_kernel<u8>",
                      "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); algorithmic bytes = 1 B "
                                   "source + 4 B output per pixel"},
         "e2e": {"value": e2e_value, "unit": "pixels/s", "h2d_bytes_per_step": int(hb.nbytes + 5 * 4 * len(org)),

@@ -41,9 +41,8 @@ namespace swift {
 namespace {
 
 constexpr int kFitThreads = 256;
-constexpr int kMeshFitThreads = 64;
+constexpr int kMeshFitThreads = 64;  // measured against 128 and 256: fewer threads, shorter FP64 reductions
 constexpr double kDetEps = 1e-9;
-constexpr int kTile = 32;
 constexpr int kMinCell = 8;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -267,15 +266,44 @@ __device__ __forceinline__ void store_px(uint8_t* p, float v) {
   *p = static_cast<uint8_t>(__float_as_int(c + 12582912.0f) - 0x4B400000);
 }
 
-// IDX: int for images below 2^31 elements (cheaper address arithmetic), else long long
+// IDX (below): int for images below 2^31 elements (cheaper address arithmetic), else long long
+// Row-run form: a thread renders kRun adjacent pixels of one row (CTA tile
+// kRunTileW x kRunTileH).  The cell and triangle walk advances one pixel at a
+// time, the triangle's record is reloaded only when it changes, and the
+// outputs leave in one vector store when the run is whole and aligned.  The
+// per-pixel arithmetic: the sample point from the record (FP32 fraction of
+// an integer base), floor and fraction, inside test with the last row and
+// column inclusive, bilinear weights.
+constexpr int kRun = 8;
+constexpr int kRunTileW = 16 * kRun;  // 16 threads per row
+constexpr int kRunTileH = 16;         // 256 threads
+
+template <typename TOut>
+__device__ __forceinline__ void store_run(TOut* p, const float (&v)[kRun]);
+template <>
+__device__ __forceinline__ void store_run<float>(float* p, const float (&v)[kRun]) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  __stcs(reinterpret_cast<float4*>(p) + 1, make_float4(v[4], v[5], v[6], v[7]));
+}
+template <>
+__device__ __forceinline__ void store_run<uint8_t>(uint8_t* p, const float (&v)[kRun]) {
+  uint32_t w[2] = {0u, 0u};
+#pragma unroll
+  for (int k = 0; k < kRun; ++k) {
+    const float c = fminf(fmaxf(v[k], 0.f), 255.f);  // NaN -> 0; half-to-even rounding below
+    w[k >> 2] |= static_cast<uint32_t>(__float_as_int(c + 12582912.0f) - 0x4B400000) << (8 * (k & 3));
+  }
+  *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+}
+
 template <typename TIn, typename TOut, typename IDX>
-__global__ void __launch_bounds__(256) render_kernel(const TIn* src, IDX src_pitch, int src_h, int src_w,
-                                                     const RenderRec* rec, swift_mesh mesh, TOut* out,
-                                                     IDX out_pitch, int out_h, int out_w, float fill) {
-  const int ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
-  // the tile's first cells (two integer divisions per CTA, shared): the
-  // threads then step from them without dividing
-  __shared__ int tile_cells[4];  // cy0, dy0, cx0, dx0
+__global__ void __launch_bounds__(256) render_run_kernel(const TIn* src, IDX src_pitch, int src_h, int src_w,
+                                                         const RenderRec* rec, swift_mesh mesh, TOut* out,
+                                                         IDX out_pitch, int out_h, int out_w, float fill,
+                                                         int vec_out) {
+  // row tiles on grid x (up to 2^20 / 16 of them), column tiles on grid y
+  const int ty0 = blockIdx.x * kRunTileH, tx0 = blockIdx.y * kRunTileW;
+  __shared__ int tile_cells[4];  // cy0, dy0, cx0, dx0 of the tile's first pixel
   if (threadIdx.x == 0) {
     auto cell_i = [&](int v, int o, int n) {
       const int d = v - o;
@@ -289,57 +317,55 @@ __global__ void __launch_bounds__(256) render_kernel(const TIn* src, IDX src_pit
     tile_cells[3] = tx0 - (mesh.origin_x + cx0 * mesh.cell);
   }
   __syncthreads();
-  const int tx = threadIdx.x & 31, tyl = threadIdx.x >> 5;
-  const int x = tx0 + tx;
-  if (x >= out_w) return;
-  // cells only advance while the offset reaches the cell side (cell >= 8: at
-  // most 4 steps across the 32-pixel tile), and stay clamped at the last cell
-  int cx = tile_cells[2], dxc = tile_cells[3] + tx;
-  while (dxc >= mesh.cell && cx < mesh.nx - 1) {
-    dxc -= mesh.cell;
-    cx += 1;
-  }
+  const int tyl = threadIdx.x >> 4, txl = threadIdx.x & 15;
+  const int y = ty0 + tyl, x0 = tx0 + kRun * txl;
+  if (y >= out_h || x0 >= out_w) return;
+  // cells advance while the offset reaches the cell side, and stay clamped
+  // at the last cell (pixels beyond the mesh use the border cells)
   int cy = tile_cells[0], dyc = tile_cells[1] + tyl;
   while (dyc >= mesh.cell && cy < mesh.ny - 1) {
     dyc -= mesh.cell;
     cy += 1;
   }
-  const float fdx = small_int_to_float(dxc);
+  int cx = tile_cells[2], dxc = tile_cells[3] + kRun * txl;
+  while (dxc >= mesh.cell && cx < mesh.nx - 1) {
+    dxc -= mesh.cell;
+    cx += 1;
+  }
+  const float fdy = small_int_to_float(dyc);
   const float cellf = small_int_to_float(mesh.cell);
-  float fdy = small_int_to_float(dyc);
-  // rows y = ty0 + tyl + 8 k: the cell advances at most once per step (cell >= 8)
-  constexpr int K = kTile / 8;
-  // phase 1: records and sample points of the thread's K pixels
-  float4 r0[K], r1[K];
+  float fdx = small_int_to_float(dxc);
+  // phase 1: the triangle walk and the sample points of the run
+  int yi[kRun], xi[kRun];
+  float fyv[kRun], fxv[kRun];
+  bool ins[kRun];
+  int cur = -1;
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < kRun; ++k) {
     if (k > 0) {
-      dyc += 8;
-      fdy += 8.0f;
-      if (dyc >= mesh.cell && cy < mesh.ny - 1) {
-        cy += 1;
-        dyc -= mesh.cell;
-        fdy -= cellf;
+      dxc += 1;
+      fdx += 1.0f;
+      if (dxc >= mesh.cell && cx < mesh.nx - 1) {
+        cx += 1;
+        dxc -= mesh.cell;
+        fdx -= cellf;
       }
     }
-    const int half = dxc >= dyc ? 0 : 1;
-    const float4* rp = reinterpret_cast<const float4*>(rec + (2 * (cy * mesh.nx + cx) + half));
-    r0[k] = __ldg(rp);      // (a_yy, a_yx, a_xy, a_xx)
-    r1[k] = __ldg(rp + 1);  // (fy, fx, by, bx)
-    r1[k].x = fmaf(r0[k].y, fdx, fmaf(r0[k].x, fdy, r1[k].x));  // local sample point
-    r1[k].y = fmaf(r0[k].w, fdx, fmaf(r0[k].z, fdy, r1[k].y));
-  }
-  int yi[K], xi[K];
-  float fyv[K], fxv[K];
-  bool ins[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const float ly = fminf(fmaxf(r1[k].x, -4e6f), 4e6f);  // |sum with the base| < 2^31; NaN -> outside
-    const float lx = fminf(fmaxf(r1[k].y, -4e6f), 4e6f);
+    const int idx = 2 * (cy * mesh.nx + cx) + (dxc >= dyc ? 0 : 1);
+    if (idx != cur) {
+      const float4* rp = reinterpret_cast<const float4*>(rec + idx);
+      r0 = __ldg(rp);      // (a_yy, a_yx, a_xy, a_xx)
+      r1 = __ldg(rp + 1);  // (fy, fx, by, bx)
+      cur = idx;
+    }
+    const float sy = fmaf(r0.y, fdx, fmaf(r0.x, fdy, r1.x));  // local sample point
+    const float sx = fmaf(r0.w, fdx, fmaf(r0.z, fdy, r1.y));
+    const float ly = fminf(fmaxf(sy, -4e6f), 4e6f);  // |sum with the base| < 2^31; NaN -> outside
+    const float lx = fminf(fmaxf(sx, -4e6f), 4e6f);
     float fy, fx;
-    int iy = __float_as_int(r1[k].z) + floor_frac(ly, fy);
-    int ix = __float_as_int(r1[k].w) + floor_frac(lx, fx);
-    // inside [0, h-1] x [0, w-1]
+    int iy = __float_as_int(r1.z) + floor_frac(ly, fy);
+    int ix = __float_as_int(r1.w) + floor_frac(lx, fx);
     const bool inside = iy >= 0 && ix >= 0 && (iy < src_h - 1 || (iy == src_h - 1 && fy == 0.f)) &&
                         (ix < src_w - 1 || (ix == src_w - 1 && fx == 0.f));
     if (iy == src_h - 1) {
@@ -356,24 +382,23 @@ __global__ void __launch_bounds__(256) render_kernel(const TIn* src, IDX src_pit
     fyv[k] = fy;
     fxv[k] = fx;
   }
-  // phase 2: all source loads in flight together
-  float sv[K][4];
+  // phase 2: every source load of the run in flight together; phase 3: interpolate
+  float v[kRun];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < kRun; ++k) {
     const TIn* s0 = src + (static_cast<IDX>(yi[k]) * src_pitch + xi[k]);
-    sv[k][0] = src_val(s0);
-    sv[k][1] = src_val(s0 + 1);
-    sv[k][2] = src_val(s0 + src_pitch);
-    sv[k][3] = src_val(s0 + src_pitch + 1);
+    const float a = src_val(s0), b = src_val(s0 + 1), c = src_val(s0 + src_pitch), d = src_val(s0 + src_pitch + 1);
+    const float top = fmaf(fxv[k], b - a, a);
+    const float bot = fmaf(fxv[k], d - c, c);
+    v[k] = ins[k] ? fmaf(fyv[k], bot - top, top) : fill;
   }
-  // phase 3: interpolate and store
+  TOut* o = out + (static_cast<IDX>(y) * out_pitch + x0);
+  if (vec_out && x0 + kRun <= out_w) {
+    store_run<TOut>(o, v);
+  } else {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int y = ty0 + tyl + 8 * k;
-    const float top = fmaf(fxv[k], sv[k][1] - sv[k][0], sv[k][0]);
-    const float bot = fmaf(fxv[k], sv[k][3] - sv[k][2], sv[k][2]);
-    const float v = ins[k] ? fmaf(fyv[k], bot - top, top) : fill;
-    if (y < out_h) store_px(out + (static_cast<IDX>(y) * out_pitch + x), v);
+    for (int k = 0; k < kRun; ++k)
+      if (x0 + k < out_w) store_px(o + k, v[k]);
   }
 }
 
@@ -443,15 +468,22 @@ extern "C" swift_status swift_render_prepare(const double* theta, const swift_me
 namespace swift {
 namespace {
 template <typename TIn, typename TOut>
-void launch_render(dim3 grid, cudaStream_t st, bool small, const TIn* src, const swift_image* im,
-                   const RenderRec* rec, const swift_mesh& mesh, TOut* out, int64_t out_pitch, int out_h, int out_w,
-                   float fill) {
+void launch_render(cudaStream_t st, bool small, const TIn* src, const swift_image* im, const RenderRec* rec,
+                   const swift_mesh& mesh, TOut* out, int64_t out_pitch, int out_h, int out_w, float fill) {
+  const dim3 grid((out_h + kRunTileH - 1) / kRunTileH, (out_w + kRunTileW - 1) / kRunTileW);
+  // a run's vector store needs its first pixel aligned to the run's bytes
+  constexpr uintptr_t kRunBytes = kRun * sizeof(TOut);
+  const int vec_out = (reinterpret_cast<uintptr_t>(out) % (kRunBytes < 16 ? kRunBytes : 16) == 0 &&
+                       (static_cast<uintptr_t>(out_pitch) * sizeof(TOut)) % (kRunBytes < 16 ? kRunBytes : 16) == 0)
+                          ? 1
+                          : 0;
   if (small)
-    render_kernel<TIn, TOut, int><<<grid, 256, 0, st>>>(src, static_cast<int>(im->pitch), im->height, im->width, rec,
-                                                        mesh, out, static_cast<int>(out_pitch), out_h, out_w, fill);
+    render_run_kernel<TIn, TOut, int><<<grid, 256, 0, st>>>(src, static_cast<int>(im->pitch), im->height, im->width,
+                                                            rec, mesh, out, static_cast<int>(out_pitch), out_h, out_w,
+                                                            fill, vec_out);
   else
-    render_kernel<TIn, TOut, long long><<<grid, 256, 0, st>>>(src, im->pitch, im->height, im->width, rec, mesh, out,
-                                                              out_pitch, out_h, out_w, fill);
+    render_run_kernel<TIn, TOut, long long><<<grid, 256, 0, st>>>(src, im->pitch, im->height, im->width, rec, mesh,
+                                                                  out, out_pitch, out_h, out_w, fill, vec_out);
 }
 }  // namespace
 }  // namespace swift
@@ -472,7 +504,6 @@ extern "C" swift_status swift_render(const swift_image* src, swift_dtype dtype, 
       static_cast<long long>(mesh->cell) * (mesh->ny > mesh->nx ? mesh->ny : mesh->nx) > (1 << 20))
     return SWIFT_ERR_INVALID_ARG;
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
-  const dim3 grid((out_w + swift::kTile - 1) / swift::kTile, (out_h + swift::kTile - 1) / swift::kTile);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const swift::RenderRec* rec = static_cast<const swift::RenderRec*>(records);
   const bool small = static_cast<long long>(src->height) * src->pitch < (1ll << 31) &&
@@ -483,14 +514,14 @@ extern "C" swift_status swift_render(const swift_image* src, swift_dtype dtype, 
   uint8_t* o8 = static_cast<uint8_t*>(out);
   if (dtype == SWIFT_IN_U8) {
     if (out_dtype == SWIFT_IN_F32)
-      swift::launch_render(grid, st, small, s8, src, rec, *mesh, of, out_pitch, out_h, out_w, fill);
+      swift::launch_render(st, small, s8, src, rec, *mesh, of, out_pitch, out_h, out_w, fill);
     else
-      swift::launch_render(grid, st, small, s8, src, rec, *mesh, o8, out_pitch, out_h, out_w, fill);
+      swift::launch_render(st, small, s8, src, rec, *mesh, o8, out_pitch, out_h, out_w, fill);
   } else {
     if (out_dtype == SWIFT_IN_F32)
-      swift::launch_render(grid, st, small, sf, src, rec, *mesh, of, out_pitch, out_h, out_w, fill);
+      swift::launch_render(st, small, sf, src, rec, *mesh, of, out_pitch, out_h, out_w, fill);
     else
-      swift::launch_render(grid, st, small, sf, src, rec, *mesh, o8, out_pitch, out_h, out_w, fill);
+      swift::launch_render(st, small, sf, src, rec, *mesh, o8, out_pitch, out_h, out_w, fill);
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
 }
