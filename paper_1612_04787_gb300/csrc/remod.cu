@@ -100,7 +100,12 @@ __global__ void zmodel_kernel(const uint8_t* stack, long long stride, int Z, int
   auto ok = [&](int j) { return valid == nullptr || __ldg(valid + j) != 0; };
   auto load = [&](int j, int (&v)[V]) {
     const uint8_t* p = col + static_cast<long long>(j) * stride;
-    if constexpr (V == 4) {
+    if constexpr (V == 16) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+      const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = (w4[i >> 2] >> (8 * (i & 3))) & 0xff;
+    } else if constexpr (V == 4) {
       const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p));
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i] = (w >> (8 * i)) & 0xff;
@@ -148,8 +153,10 @@ __global__ void zmodel_kernel(const uint8_t* stack, long long stride, int Z, int
         const int s = S[i] - (vz ? c[i] : 0);
         o[i] = n > 0 ? __fdiv_rn(static_cast<float>(s), static_cast<float>(n)) : static_cast<float>(c[i]);
       }
-      if constexpr (V == 4) {
-        __stcs(reinterpret_cast<float4*>(op), make_float4(o[0], o[1], o[2], o[3]));
+      if constexpr (V >= 4) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4)
+          __stcs(reinterpret_cast<float4*>(op + i), make_float4(o[i], o[i + 1], o[i + 2], o[i + 3]));
       } else {
         __stcs(op, o[0]);
       }
@@ -161,7 +168,13 @@ __global__ void zmodel_kernel(const uint8_t* stack, long long stride, int Z, int
         o[i] = n > 0 ? round_half_even_div(static_cast<uint32_t>(s), static_cast<uint32_t>(n))
                      : static_cast<uint32_t>(c[i]);
       }
-      if constexpr (V == 4) {
+      if constexpr (V == 16) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          w4[i] = o[4 * i] | (o[4 * i + 1] << 8) | (o[4 * i + 2] << 16) | (o[4 * i + 3] << 24);
+        *reinterpret_cast<uint4*>(op) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      } else if constexpr (V == 4) {
         *reinterpret_cast<uint32_t*>(op) = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
       } else {
         *op = static_cast<uint8_t>(o[0]);
@@ -232,10 +245,18 @@ extern "C" swift_status swift_zmodel(const uint8_t* stack, int64_t stride, int32
   const int oalign = f32 ? 15 : 3;  // 16-byte float4 / 4-byte packed stores
   const bool vec = width % 4 == 0 && pitch % 4 == 0 && stride % 4 == 0 && out_pitch % 4 == 0 && out_stride % 4 == 0 &&
                    (reinterpret_cast<uintptr_t>(stack) & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & oalign) == 0;
+  // 16 pixels per thread when every row and section start is 16-byte aligned (input and output)
+  const bool vec16 = vec && width % 16 == 0 && pitch % 16 == 0 && stride % 16 == 0 && out_pitch % 16 == 0 &&
+                     out_stride % 16 == 0 && (reinterpret_cast<uintptr_t>(stack) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(out) & 15) == 0;
   const dim3 grid_v((width / 4 + 127) / 128, height), grid_s((width + 127) / 128, height);
+  const dim3 grid_16((width / 16 + 127) / 128, height);
   if (f32) {
     float* o = static_cast<float*>(out);
-    if (vec)
+    if (vec16)
+      swift::zmodel_kernel<16, float><<<grid_16, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
+                                                               valid, o, out_stride, out_pitch);
+    else if (vec)
       swift::zmodel_kernel<4, float><<<grid_v, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
                                                              valid, o, out_stride, out_pitch);
     else
@@ -243,7 +264,10 @@ extern "C" swift_status swift_zmodel(const uint8_t* stack, int64_t stride, int32
                                                              valid, o, out_stride, out_pitch);
   } else {
     uint8_t* o = static_cast<uint8_t*>(out);
-    if (vec)
+    if (vec16)
+      swift::zmodel_kernel<16, uint8_t><<<grid_16, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
+                                                                 valid, o, out_stride, out_pitch);
+    else if (vec)
       swift::zmodel_kernel<4, uint8_t><<<grid_v, 128, 0, st>>>(stack, stride, n_sections, height, width, pitch, k,
                                                                valid, o, out_stride, out_pitch);
     else

@@ -42,7 +42,7 @@ def test_downsample_float32_bit_exact(f):
 
 
 @pytest.mark.parametrize("k", [1, 4])
-@pytest.mark.parametrize("width", [256, 257])  # vector and scalar paths
+@pytest.mark.parametrize("width", [256, 260, 257])  # 16-pixel, 4-pixel and scalar paths
 def test_zmodel_bit_exact(k, width):
     rng = np.random.default_rng(k + width)
     stack = rng.integers(0, 256, (9, 40, width)).astype(np.uint8)
@@ -71,7 +71,7 @@ def test_zmodel_feeds_the_match_as_a_reference():
     assert np.abs(r_model["sy"]).max() < 2.0 and np.abs(r_model["sx"]).max() < 2.0
 
 
-@pytest.mark.parametrize("width", [256, 257])
+@pytest.mark.parametrize("width", [256, 260, 257])  # 16-pixel, 4-pixel and scalar paths
 def test_zmodel_uint8_bit_exact(width):
     rng = np.random.default_rng(width)
     stack = rng.integers(0, 256, (7, 33, width)).astype(np.uint8)
