@@ -29,21 +29,34 @@ __device__ __forceinline__ uint32_t round_half_even_div(uint32_t s, uint32_t d) 
 }
 
 // uint8, f = 2 or 4, four outputs per thread from 8- or 16-byte row loads
-template <int F>
+template <int F, int OUT>
 __global__ void downsample_u8_vec_kernel(const uint8_t* src, long long pitch, long long stride, uint8_t* out,
                                          long long out_pitch, long long out_stride, int H, int W) {
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  // OUT outputs per thread from F rows of F * OUT bytes (8 or 16-byte loads)
+  static_assert((F == 2 && (OUT == 4 || OUT == 8)) || (F == 4 && OUT == 4), "vector shapes");
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * OUT;
   const int y = blockIdx.y;
   if (x0 >= W) return;
   const uint8_t* b = src + blockIdx.z * stride + static_cast<long long>(F) * y * pitch + static_cast<long long>(F) * x0;
-  uint32_t sum[4] = {0u, 0u, 0u, 0u};
+  uint32_t sum[OUT];
+#pragma unroll
+  for (int o = 0; o < OUT; ++o) sum[o] = 0u;
 #pragma unroll
   for (int i = 0; i < F; ++i) {
-    if constexpr (F == 2) {
+    if constexpr (F == 2 && OUT == 4) {
       const uint2 v = __ldg(reinterpret_cast<const uint2*>(b + i * pitch));
       const uint32_t w[2] = {v.x, v.y};
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
+        const uint32_t word = w[o >> 1];
+        const int sh = 16 * (o & 1);
+        sum[o] += ((word >> sh) & 0xffu) + ((word >> (sh + 8)) & 0xffu);
+      }
+    } else if constexpr (F == 2) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(b + i * pitch));
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
         const uint32_t word = w[o >> 1];
         const int sh = 16 * (o & 1);
         sum[o] += ((word >> sh) & 0xffu) + ((word >> (sh + 8)) & 0xffu);
@@ -56,10 +69,18 @@ __global__ void downsample_u8_vec_kernel(const uint8_t* src, long long pitch, lo
         sum[o] += (w[o] & 0xffu) + ((w[o] >> 8) & 0xffu) + ((w[o] >> 16) & 0xffu) + (w[o] >> 24);
     }
   }
-  uint32_t packed = 0u;
+  uint32_t packed[OUT / 4];
 #pragma unroll
-  for (int o = 0; o < 4; ++o) packed |= round_half_even_div(sum[o], F * F) << (8 * o);
-  *reinterpret_cast<uint32_t*>(out + blockIdx.z * out_stride + static_cast<long long>(y) * out_pitch + x0) = packed;
+  for (int o = 0; o < OUT; ++o) {
+    const uint32_t r = round_half_even_div(sum[o], F * F) << (8 * (o & 3));
+    packed[o >> 2] = (o & 3) ? (packed[o >> 2] | r) : r;
+  }
+  uint8_t* op = out + blockIdx.z * out_stride + static_cast<long long>(y) * out_pitch + x0;
+  if constexpr (OUT == 8) {
+    *reinterpret_cast<uint2*>(op) = make_uint2(packed[0], packed[1]);
+  } else {
+    *reinterpret_cast<uint32_t*>(op) = packed[0];
+  }
 }
 
 template <typename T>
@@ -208,14 +229,22 @@ extern "C" swift_status swift_downsample(const swift_image* src, swift_dtype dty
                      (src->count == 1 || src->stride % (4 * F) == 0) &&
                      (reinterpret_cast<uintptr_t>(s8) % (4 * F)) == 0 && out_pitch % 4 == 0 &&
                      (reinterpret_cast<uintptr_t>(o8) % 4) == 0;
-    if (vec) {
+    // 2x: eight outputs per thread from 16-byte loads when the rows allow it
+    const bool vec8 = vec && F == 2 && W % 8 == 0 && src->pitch % 16 == 0 &&
+                      (src->count == 1 || src->stride % 16 == 0) && (reinterpret_cast<uintptr_t>(s8) % 16) == 0 &&
+                      out_pitch % 8 == 0 && (reinterpret_cast<uintptr_t>(o8) % 8) == 0;
+    if (vec8) {
+      const dim3 grid((W / 8 + 127) / 128, H, src->count);
+      swift::downsample_u8_vec_kernel<2, 8><<<grid, 128, 0, st>>>(s8, src->pitch, src->stride, o8, out_pitch,
+                                                                  out_stride, H, W);
+    } else if (vec) {
       const dim3 grid((W / 4 + 127) / 128, H, src->count);
       if (F == 2)
-        swift::downsample_u8_vec_kernel<2><<<grid, 128, 0, st>>>(s8, src->pitch, src->stride, o8, out_pitch,
-                                                                 out_stride, H, W);
+        swift::downsample_u8_vec_kernel<2, 4><<<grid, 128, 0, st>>>(s8, src->pitch, src->stride, o8, out_pitch,
+                                                                    out_stride, H, W);
       else
-        swift::downsample_u8_vec_kernel<4><<<grid, 128, 0, st>>>(s8, src->pitch, src->stride, o8, out_pitch,
-                                                                 out_stride, H, W);
+        swift::downsample_u8_vec_kernel<4, 4><<<grid, 128, 0, st>>>(s8, src->pitch, src->stride, o8, out_pitch,
+                                                                    out_stride, H, W);
     } else {
       const dim3 grid((W + 255) / 256, H, src->count);
       swift::downsample_kernel<uint8_t><<<grid, 256, 0, st>>>(s8, src->pitch, src->stride, o8, out_pitch,

@@ -33,6 +33,15 @@ def test_downsample_uint8_batch_vector_path(f):
         np.testing.assert_array_equal(got[z], remod.downsample(stack[z], f))
 
 
+@pytest.mark.parametrize("width", [264, 256])  # 2x: four outputs per thread (W = 132), eight (W = 128)
+def test_downsample_uint8_2x_vector_widths(width):
+    rng = np.random.default_rng(width)
+    img = rng.integers(0, 256, (2, 40, width)).astype(np.uint8)
+    got = swift.downsample(torch.from_numpy(img).to(DEV), 2).cpu().numpy()
+    for z in range(2):
+        np.testing.assert_array_equal(got[z], remod.downsample(img[z], 2))
+
+
 @pytest.mark.parametrize("f", [2, 4])
 def test_downsample_float32_bit_exact(f):
     rng = np.random.default_rng(f)
