@@ -335,6 +335,14 @@ swift_status swift_correspondences(const swift_result* results, const int32_t* r
 swift_status swift_fit_affine(const float* q, const float* p, const float* w, const int64_t* offsets,
                               int32_t n_groups, double* theta, int32_t* status, void* stream);
 
+/* The same fit as an update: theta holds each group's previous affine on
+ * entry; an OK group overwrites it, a degenerate group keeps it (status
+ * SWIFT_FIT_DEGENERATE).  This is how the registration loop keeps a section's
+ * affine when its matches do not support a new one, without a host round
+ * trip.  Same arguments and errors as swift_fit_affine. */
+swift_status swift_fit_affine_update(const float* q, const float* p, const float* w, const int64_t* offsets,
+                                     int32_t n_groups, double* theta, int32_t* status, void* stream);
+
 /* One affine per mesh triangle (theta: device double [2 ny nx][6], status:
  * device int32 [2 ny nx]), each fitted to the points within Chebyshev
  * distance `band` (>= 0, output pixels) of the closed triangle: the

@@ -320,10 +320,13 @@ def correspondences(res, ref_origin, mov_origin, n: int, min_snr: float = 0.0, s
     return q, p, w
 
 
-def fit_affine(q, p, w, offsets=None, stream=None):
+def fit_affine(q, p, w, offsets=None, stream=None, update=None, status=None):
     """Weighted least-squares affines p ~ A q + t, one per group of points
     (``offsets`` int64 [G + 1], default one group).  Returns (theta [G, 6]
-    float64, status [G] int32) on the device."""
+    float64, status [G] int32) on the device.  ``update``: a contiguous
+    float64 [G, 6] device tensor of previous affines, overwritten in place
+    where a group's fit is OK and kept where it is degenerate (returned as
+    theta); ``status``: an int32 [G] device tensor to write into."""
     _dev(q, torch.float32, (2,), "q")
     _dev(p, torch.float32, (2,), "p")
     if w.shape[0] != q.shape[0] or p.shape[0] != q.shape[0]:
@@ -331,10 +334,20 @@ def fit_affine(q, p, w, offsets=None, stream=None):
     if offsets is None:
         offsets = torch.tensor([0, q.shape[0]], dtype=torch.int64, device=q.device)
     G = int(offsets.shape[0]) - 1
-    theta = torch.empty((G, 6), dtype=torch.float64, device=q.device)
-    status = torch.empty((G,), dtype=torch.int32, device=q.device)
-    check(lib.swift_fit_affine(q.data_ptr(), p.data_ptr(), w.data_ptr(), offsets.data_ptr(), G, theta.data_ptr(),
-                               status.data_ptr(), _stream_ptr(stream)), "swift_fit_affine")
+    if update is not None:
+        if update.dtype != torch.float64 or tuple(update.shape) != (G, 6) or not update.is_contiguous():
+            raise ValueError("update must be a contiguous float64 [G, 6] tensor")
+        theta = update
+    else:
+        theta = torch.empty((G, 6), dtype=torch.float64, device=q.device)
+    if status is None:
+        status = torch.empty((G,), dtype=torch.int32, device=q.device)
+    elif status.dtype != torch.int32 or tuple(status.shape) != (G,) or not status.is_contiguous():
+        raise ValueError("status must be a contiguous int32 [G] tensor")
+    fn, name = ((lib.swift_fit_affine_update, "swift_fit_affine_update") if update is not None
+                else (lib.swift_fit_affine, "swift_fit_affine"))
+    check(fn(q.data_ptr(), p.data_ptr(), w.data_ptr(), offsets.data_ptr(), G, theta.data_ptr(), status.data_ptr(),
+             _stream_ptr(stream)), name)
     return theta, status
 
 

@@ -46,6 +46,7 @@ EXPORTS = (
     "swift_version",
     "swift_correspondences",
     "swift_fit_affine",
+    "swift_fit_affine_update",
     "swift_mesh_fit",
     "swift_render_prepare",
     "swift_render",
@@ -131,6 +132,9 @@ def _load():
     lib.swift_fit_affine.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                                      C.c_void_p, C.c_void_p]
     lib.swift_fit_affine.restype = C.c_int
+    lib.swift_fit_affine_update.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
+    lib.swift_fit_affine_update.restype = C.c_int
     lib.swift_mesh_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(SwiftMesh), C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p]
     lib.swift_mesh_fit.restype = C.c_int

@@ -4,13 +4,14 @@ settles.
 
 Every image step is a library kernel: uint8 Z models (``swift_zmodel``),
 the grid match of each raw section against its model (``swift_match_batch``),
-SNR-weighted correspondences and the least-squares affine
-(``swift_correspondences``, ``swift_fit_affine``), and the render of the raw
-section through that affine (``swift_render_prepare`` / ``swift_render``,
-uint8).  The host only sequences the calls, keeps a section's previous
-affine when its fit is degenerate, and applies the convergence rule on the
-median SNR of each iteration (read back from the results), as the paper's
-own driver scripts did around its modules.
+SNR-weighted correspondences and the least-squares affine, which keeps a
+section's previous affine when its fit is degenerate
+(``swift_correspondences``, ``swift_fit_affine_update``), and the render of
+the raw section through that affine (``swift_render_prepare`` /
+``swift_render``, uint8).  The host only sequences the calls (or replays
+them as one CUDA graph) and applies the convergence rule on the median SNR
+of each iteration (read back from the results), as the paper's own driver
+scripts did around its modules.
 
 Readings (the same as the oracle's): a section whose fit is degenerate keeps
 its previous affine; the loop stops when the median SNR of the OK windows
@@ -23,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import FIT_OK, Level, Mesh, Plan, correspondences, decode, fit_affine, render, render_records, zmodel
+from . import Level, Mesh, Plan, correspondences, decode, fit_affine, render, render_records, zmodel
 
 
 def window_grid(h: int, w: int, n: int, stride: int) -> np.ndarray:
@@ -34,53 +35,98 @@ def window_grid(h: int, w: int, n: int, stride: int) -> np.ndarray:
     return np.stack([Y.ravel(), X.ravel()], 1).astype(np.int32)
 
 
-def align_stack(raw: torch.Tensor, level: Level, stride: int, k: int, iters: int, tol: float = 0.0,
-                min_snr: float = 0.0, stream=None):
-    """Align a uint8 [Z, H, W] CUDA stack.  Returns (aligned uint8 [Z, H, W],
-    theta float64 [Z, 6] (model frame -> raw section: p = A q + t), list of
-    the median SNR of every iteration).
+class StackAligner:
+    """The registration loop for stacks of one shape, reusable: it owns the
+    plan, the buffers and (with ``graph``) one captured CUDA graph of an
+    iteration.  An iteration: the Z models, every section's grid match (one
+    call per section), one correspondence call and one grouped affine update
+    over all sections (a degenerate fit keeps the section's previous affine on
+    the device), and the renders; then one read-back of the match results for
+    the convergence rule.  The very first iteration runs call by call, the
+    second is captured, and every later iteration (of this run or of later
+    runs) is one replay of that graph: a run copies its stack into the
+    aligner's own buffer, so the graph's pointers stay valid.  Runs on the
+    current CUDA stream."""
 
-    Per iteration: the Z models, then every section's grid match (one call per
-    section), then one correspondence call and one grouped fit over all
-    sections, one read-back of the fit statuses and the match results, and
-    the renders.  A section's match and fit depend only on the models built at
-    the start of the iteration, so queueing them all before the read-back
-    gives the same affines as handling the sections one by one."""
+    def __init__(self, Z: int, H: int, W: int, level: Level, stride: int, k: int, min_snr: float = 0.0,
+                 device=None, graph: bool = True):
+        dev = torch.device(device if device is not None else "cuda")
+        self.Z, self.H, self.W, self.k, self.min_snr, self.graph = Z, H, W, k, min_snr, graph
+        self.n = level.n
+        org = torch.from_numpy(window_grid(H, W, level.n, stride)).to(dev)
+        self.B = B = int(org.shape[0])
+        self.org, self.org_all = org, org.repeat(Z, 1)  # the same grid in every section
+        self.offsets = torch.arange(0, (Z + 1) * B, B, dtype=torch.int64, device=dev)
+        self.plan = Plan([level], dtype="u8", max_windows=B)
+        self.raw = torch.empty((Z, H, W), dtype=torch.uint8, device=dev)
+        self.aligned = torch.empty_like(self.raw)
+        self.model = torch.empty_like(self.raw)
+        self.identity = torch.tensor([1.0, 0.0, 0.0, 0.0, 1.0, 0.0], dtype=torch.float64, device=dev).repeat(Z, 1)
+        self.theta = self.identity.clone()
+        self.status = torch.empty((Z,), dtype=torch.int32, device=dev)
+        self.mesh = Mesh(0, 0, max(H, W), 1, 1)
+        nt = self.mesh.n_triangles
+        self.tri = torch.empty((Z, nt, 6), dtype=torch.float64, device=dev)  # both triangles: the section's affine
+        self.recs = torch.empty((Z, nt, 8), dtype=torch.float32, device=dev)
+        self.res = torch.empty((Z, B, 8), dtype=torch.int32, device=dev)
+        self.g = None
+        self.iterations_done = 0
+
+    def _iteration(self):
+        Z, B, n, nt = self.Z, self.B, self.n, self.mesh.n_triangles
+        zmodel(self.aligned, self.k, out=self.model)
+        for z in range(Z):
+            self.plan.match(self.model[z], self.raw[z], self.org, self.org, out=self.res[z])
+        q, p, w = correspondences(self.res.view(Z * B, 8), self.org_all, self.org_all, n, self.min_snr)
+        fit_affine(q, p, w, offsets=self.offsets, update=self.theta, status=self.status)
+        self.tri.copy_(self.theta[:, None, :].expand(Z, nt, 6))
+        for z in range(Z):
+            render_records(self.tri[z], self.mesh, records=self.recs[z])
+            render(self.raw[z], self.tri[z], self.mesh, self.H, self.W, fill=0.0, out=self.aligned[z],
+                   records=self.recs[z])
+
+    def _step(self):
+        dev = self.raw.device
+        if self.g is not None:
+            self.g.replay()
+        elif self.graph and self.iterations_done >= 1:
+            self.g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.graph(self.g, stream=side):
+                self._iteration()
+            torch.cuda.current_stream(dev).wait_stream(side)
+            self.g.replay()
+        else:
+            self._iteration()
+        self.iterations_done += 1
+
+    def run(self, raw: torch.Tensor, iters: int, tol: float = 0.0):
+        """Align ``raw`` (uint8 [Z, H, W] on the aligner's device).  Returns
+        (aligned uint8 [Z, H, W], theta float64 [Z, 6] (model frame -> raw
+        section: p = A q + t), list of the median SNR of every iteration)."""
+        if raw.dtype != torch.uint8 or tuple(raw.shape) != (self.Z, self.H, self.W) or raw.device != self.raw.device:
+            raise TypeError("raw must be a uint8 [Z, H, W] tensor of this aligner's shape and device")
+        self.raw.copy_(raw)
+        self.aligned.copy_(raw)
+        self.theta.copy_(self.identity)
+        hist = []
+        for _ in range(iters):
+            self._step()
+            d = decode(self.res.view(self.Z * self.B, 8))
+            good = (d["status"] == 0) & np.isfinite(d["snr"])
+            hist.append(float(np.median(d["snr"][good])) if good.any() else 0.0)
+            if len(hist) > 1 and abs(hist[-1] - hist[-2]) <= tol * abs(hist[-2]):
+                break
+        return self.aligned.clone(), self.theta.clone(), hist
+
+
+def align_stack(raw: torch.Tensor, level: Level, stride: int, k: int, iters: int, tol: float = 0.0,
+                min_snr: float = 0.0, graph: bool = True):
+    """Align a uint8 [Z, H, W] CUDA stack once (a StackAligner made for it).
+    Returns (aligned uint8 [Z, H, W], theta float64 [Z, 6], list of the median
+    SNR of every iteration)."""
     if raw.dtype != torch.uint8 or raw.dim() != 3 or not raw.is_cuda or not raw.is_contiguous():
         raise TypeError("raw must be a contiguous uint8 [Z, H, W] CUDA tensor")
     Z, H, W = raw.shape
-    dev = raw.device
-    n = level.n
-    org = torch.from_numpy(window_grid(H, W, n, stride)).to(dev)
-    B = int(org.shape[0])
-    org_all = org.repeat(Z, 1)  # the same grid in every section
-    offsets = torch.arange(0, (Z + 1) * B, B, dtype=torch.int64, device=dev)
-    plan = Plan([level], dtype="u8", max_windows=B)
-    aligned = raw.clone()
-    model = torch.empty_like(raw)
-    theta = torch.tensor([1.0, 0.0, 0.0, 0.0, 1.0, 0.0], dtype=torch.float64, device=dev).repeat(Z, 1)
-    mesh = Mesh(0, 0, max(H, W), 1, 1)
-    recs = torch.empty((mesh.n_triangles, 8), dtype=torch.float32, device=dev)
-    res = torch.empty((Z, B, 8), dtype=torch.int32, device=dev)
-    hist = []
-    for _ in range(iters):
-        zmodel(aligned, k, out=model, stream=stream)
-        for z in range(Z):
-            plan.match(model[z], raw[z], org, org, out=res[z], stream=stream)
-        q, p, w = correspondences(res.view(Z * B, 8), org_all, org_all, n, min_snr, stream=stream)
-        th, st = fit_affine(q, p, w, offsets=offsets, stream=stream)
-        if stream is not None:
-            stream.synchronize()
-        ok = st.cpu().numpy() == FIT_OK  # a degenerate fit keeps the section's previous affine
-        d = decode(res.view(Z * B, 8))
-        for z in range(Z):
-            if ok[z]:
-                theta[z] = th[z]
-            tri = theta[z].repeat(mesh.n_triangles, 1)
-            render_records(tri, mesh, records=recs, stream=stream)
-            render(raw[z], tri, mesh, H, W, fill=0.0, out=aligned[z], records=recs, stream=stream)
-        good = (d["status"] == 0) & np.isfinite(d["snr"])
-        hist.append(float(np.median(d["snr"][good])) if good.any() else 0.0)
-        if len(hist) > 1 and abs(hist[-1] - hist[-2]) <= tol * abs(hist[-2]):
-            break
-    return aligned, theta, hist
+    return StackAligner(Z, H, W, level, stride, k, min_snr, raw.device, graph).run(raw, iters, tol)

@@ -121,9 +121,11 @@ __device__ void write_identity(double* th) {
   th[0] = 1.0, th[1] = 0.0, th[2] = 0.0, th[3] = 0.0, th[4] = 1.0, th[5] = 0.0;
 }
 
+// keep: a degenerate group leaves its theta as it was (an update of previous
+// affines) instead of writing the identity
 __global__ void __launch_bounds__(kFitThreads) fit_groups_kernel(const float* q, const float* p, const float* w,
                                                                  const int64_t* offsets, double* theta,
-                                                                 int32_t* status) {
+                                                                 int32_t* status, int keep) {
   __shared__ double sh[kFitThreads / 32][12];
   const int g = blockIdx.x;
   const int64_t b = offsets[g], e = offsets[g + 1];
@@ -139,7 +141,8 @@ __global__ void __launch_bounds__(kFitThreads) fit_groups_kernel(const float* q,
     double th[6];
     int st = solve_affine(m, cy, cx, th);
     if (st != SWIFT_FIT_OK) write_identity(th);
-    for (int k = 0; k < 6; ++k) theta[6 * g + k] = th[k];
+    if (st == SWIFT_FIT_OK || !keep)
+      for (int k = 0; k < 6; ++k) theta[6 * g + k] = th[k];
     status[g] = st;
   }
 }
@@ -428,15 +431,28 @@ bool mesh_ok(const swift_mesh* m) {
 
 }  // namespace swift
 
-extern "C" swift_status swift_fit_affine(const float* q, const float* p, const float* w, const int64_t* offsets,
-                                         int32_t n_groups, double* theta, int32_t* status, void* stream) {
+namespace {
+swift_status fit_affine_impl(const float* q, const float* p, const float* w, const int64_t* offsets,
+                             int32_t n_groups, double* theta, int32_t* status, int keep, void* stream) {
   if (n_groups < 0) return SWIFT_ERR_INVALID_ARG;
   if (n_groups == 0) return SWIFT_OK;
   if (!q || !p || !w || !offsets || !theta || !status) return SWIFT_ERR_INVALID_ARG;
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
-  swift::fit_groups_kernel<<<n_groups, swift::kFitThreads, 0, static_cast<cudaStream_t>(stream)>>>(q, p, w, offsets,
-                                                                                                     theta, status);
+  swift::fit_groups_kernel<<<n_groups, swift::kFitThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      q, p, w, offsets, theta, status, keep);
   return cudaGetLastError() == cudaSuccess ? SWIFT_OK : SWIFT_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" swift_status swift_fit_affine(const float* q, const float* p, const float* w, const int64_t* offsets,
+                                         int32_t n_groups, double* theta, int32_t* status, void* stream) {
+  return fit_affine_impl(q, p, w, offsets, n_groups, theta, status, 0, stream);
+}
+
+extern "C" swift_status swift_fit_affine_update(const float* q, const float* p, const float* w,
+                                                const int64_t* offsets, int32_t n_groups, double* theta,
+                                                int32_t* status, void* stream) {
+  return fit_affine_impl(q, p, w, offsets, n_groups, theta, status, 1, stream);
 }
 
 extern "C" swift_status swift_mesh_fit(const float* q, const float* p, const float* w, int64_t n_points,

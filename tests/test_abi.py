@@ -88,4 +88,6 @@ def test_mir_argument_errors_before_any_launch():
     assert lib.swift_render(C.byref(img), 0, dummy, C.byref(good), dummy, 7, 8, 8, 8, 0.0, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_fit_affine(dummy, dummy, dummy, dummy, -1, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_fit_affine(None, None, None, None, 0, None, None, None) == _lib.SWIFT_OK
+    assert lib.swift_fit_affine_update(dummy, dummy, dummy, dummy, -1, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
+    assert lib.swift_fit_affine_update(None, None, None, None, 0, None, None, None) == _lib.SWIFT_OK
     assert lib.swift_correspondences(None, None, None, 4, 64, 0.0, None, None, None, None) == _lib.SWIFT_ERR_INVALID_ARG

@@ -67,6 +67,29 @@ def test_fit_affine_groups_match_oracle():
         np.testing.assert_allclose(th[g], ot, rtol=1e-9, atol=1e-7 * (1 + np.abs(ot).max()))
 
 
+def test_fit_affine_update_keeps_previous_affines_of_degenerate_groups():
+    """The update form: an OK group is overwritten by its fit (the oracle's),
+    a degenerate group (all weights 0, or collinear points) keeps what theta
+    held."""
+    rng = np.random.default_rng(17)
+    q = rng.uniform(0, 2000, (60, 2)).astype(np.float32)
+    p = (q + rng.normal(0, 1, (60, 2)) + 5).astype(np.float32)
+    w = rng.uniform(0.5, 3, 60).astype(np.float32)
+    w[20:40] = 0.0                    # group 1: no weight
+    q[40:60, 1] = q[40:60, 0]         # group 2: collinear
+    offsets = np.array([0, 20, 40, 60], np.int64)
+    prev = rng.normal(0, 1, (3, 6))
+    theta = T(prev.copy())
+    th, st = swift.fit_affine(T(q), T(p), T(w), offsets=T(offsets), update=theta)
+    assert th.data_ptr() == theta.data_ptr()
+    th, st = th.cpu().numpy(), st.cpu().numpy()
+    ot, os_ = mir.fit_affine(q[:20], p[:20], w[:20])
+    assert st[0] == os_ == swift.FIT_OK
+    np.testing.assert_allclose(th[0], ot, rtol=1e-9, atol=1e-7)
+    assert (st[1:] == mir.DEGENERATE).all()
+    np.testing.assert_array_equal(th[1:], prev[1:])
+
+
 @pytest.mark.parametrize("band", [0, 64, 128])
 def test_mesh_fit_matches_oracle(band):
     rng = np.random.default_rng(11 + band)
