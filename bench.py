@@ -1179,7 +1179,9 @@ def main():
                     "pipeline_tflops": step_tflops, "pipeline_frac": step_tflops / peak}
     line = {
         "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world, "steps": args.steps,
-        "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": warm, "ms_per_step": total_ms / args.steps,
+        "ms_per_step_best": min(durs), "ms_per_step_median": statistics.median(durs),  # this rank's steps
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x2": "bf16x2 (f32 accumulate)",
                                                          "fp16x2": "f16x2 (f32 accumulate)"}[args.precision],
         "data": "synthetic",
