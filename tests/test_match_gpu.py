@@ -170,6 +170,26 @@ def test_float_sections_aligned_and_unaligned_origins(sections, n):
     check_sections(fa.astype(np.float64), fb.astype(np.float64), ro, mo, lv, g, f"float sections n={n}")
 
 
+def test_full_size_section_pair_sampled_parity():
+    """The benchmark's workload at full size and in its launch configuration:
+    the 31 x 31 grid of 256^2 windows (stride 128) on the 4096^2 uint8 section
+    pair with the bench's seeds, in one call.  96 sampled windows against the
+    oracle; for every window, properties that hold at any size."""
+    a, b = synth.em_section_pair(4096, seed_content=0, seed_warp=1, seed_noise=(2, 3))
+    org = synth.grid_origins(4096, 256, 128).astype(np.int32)
+    assert len(org) == 961
+    lv = swift.Level(256, 0.65, "hann", 1.0, 3.0)
+    g = run_sections(a, b, org, org, lv)
+    assert (g["status"] == 0).all()
+    assert ((g["dy"] >= -128) & (g["dy"] < 128) & (g["dx"] >= -128) & (g["dx"] < 128)).all()
+    assert (np.abs(g["sy"] - g["dy"]) <= 0.5).all() and (np.abs(g["sx"] - g["dx"]) <= 0.5).all()
+    assert np.isfinite(g["snr"]).all() and (g["snr"] > 0).all() and (g["peak"] > 0).all()
+    olv = oracle_level(lv)
+    for i in np.random.default_rng(961).choice(961, 96, replace=False):
+        o, tied = oracle_window(swim.gather(b, org[i], 256), swim.gather(a, org[i], 256), olv)
+        compare(g, int(i), o, tied, 256, "full-size sections")
+
+
 def test_projection_reference(sections):
     a, b = sections
     n = 128
