@@ -31,6 +31,20 @@ namespace swift {
 // ---------------------------------------------------------------------------
 // BP: prepare float32 windows (affine resampling / gather / projection)
 // ---------------------------------------------------------------------------
+// Warped sample position of window pixel (i, j) in the moving section, as an
+// exact integer base (the window centre, origin + n/2) plus a small FP32
+// local offset a (i - n/2, j - n/2) + t (|offset| < ~n): its rounding stays
+// near 1e-5 px, where adding it to a section coordinate would round to
+// ~2e-4 px at 4096 and move samples across pixel lines (where the bilinear
+// derivative jumps).  Gives the top-left tap, clamped to the last row or
+// column pair, and the fraction from it.
+__device__ __forceinline__ void warp_tap(int base, float local, int last_pair, int& t0, float& f) {
+  const float fl = floorf(local);
+  const int t = base + static_cast<int>(fl);
+  t0 = min(t, last_pair);
+  f = (local - fl) + static_cast<float>(t - t0);
+}
+
 template <int N, typename TIn>
 __global__ void __launch_bounds__(256) prep_kernel(const MatchLaunch L, const BackLaunch K, const BackWork BW,
                                                    long long b0) {
@@ -51,14 +65,16 @@ __global__ void __launch_bounds__(256) prep_kernel(const MatchLaunch L, const Ba
     for (int k = 0; k < 6; ++k) th[k] = __ldg(K.affine + 6 * b + k);
   }
   const float c = 0.5f * N;
+  const int cy = my + N / 2, cx = mx + N / 2;  // window centre: the integer base of every sample
   // bounds: the reference window, and the four corners of the warped moving window
   bool ok = !(ry < 0 || rx < 0 || ry > L.ref_h - N || rx > L.ref_w - N);
 #pragma unroll
   for (int corner = 0; corner < 4; ++corner) {
     const float di = (corner & 1 ? N - 1 : 0) - c, dj = (corner & 2 ? N - 1 : 0) - c;
-    const float Y = my + c + th[0] * di + th[1] * dj + th[2];
-    const float X = mx + c + th[3] * di + th[4] * dj + th[5];
-    ok = ok && Y >= 0.f && X >= 0.f && Y <= static_cast<float>(L.mov_h - 1) && X <= static_cast<float>(L.mov_w - 1);
+    const float ly = th[0] * di + th[1] * dj + th[2];
+    const float lx = th[3] * di + th[4] * dj + th[5];
+    ok = ok && ly >= static_cast<float>(-cy) && lx >= static_cast<float>(-cx) &&
+         ly <= static_cast<float>(L.mov_h - 1 - cy) && lx <= static_cast<float>(L.mov_w - 1 - cx);
   }
   if (rb == 0 && tid == 0) BW.pre_status[s] = ok ? SWIFT_WIN_OK : SWIFT_WIN_OUT_OF_BOUNDS;
   if (!ok) return;
@@ -75,11 +91,10 @@ __global__ void __launch_bounds__(256) prep_kernel(const MatchLaunch L, const Ba
     rp[i * N + j] = L.ref_count > 1 ? rv * inv_k : rv;
     // moving: bilinear sample at the warped position
     const float di = i - c, dj = j - c;
-    const float Y = my + c + th[0] * di + th[1] * dj + th[2];
-    const float X = mx + c + th[3] * di + th[4] * dj + th[5];
-    const int y0 = min(static_cast<int>(floorf(Y)), L.mov_h - 2);
-    const int x0 = min(static_cast<int>(floorf(X)), L.mov_w - 2);
-    const float fy = Y - y0, fx = X - x0;
+    int y0, x0;
+    float fy, fx;
+    warp_tap(cy, th[0] * di + th[1] * dj + th[2], L.mov_h - 2, y0, fy);
+    warp_tap(cx, th[3] * di + th[4] * dj + th[5], L.mov_w - 2, x0, fx);
     const TIn* p = mov + static_cast<long long>(y0) * L.mov_pitch + x0;
     const float s00 = load_px<TIn>(p), s01 = load_px<TIn>(p + 1);
     const float s10 = load_px<TIn>(p + L.mov_pitch), s11 = load_px<TIn>(p + L.mov_pitch + 1);
@@ -500,6 +515,7 @@ __global__ void __launch_bounds__(256) back_affine_kernel(const MatchLaunch L, c
   }
   const int my = __ldg(L.mov_origin + 2 * b), mx = __ldg(L.mov_origin + 2 * b + 1);
   const float c = 0.5f * N;
+  const int cy = my + N / 2, cx = mx + N / 2;  // window centre: the integer base of every sample
   const TIn* mov = static_cast<const TIn*>(L.mov);
   const float* gmp = reinterpret_cast<const float*>(BW.fw.zr + s * N * N);
   __syncthreads();
@@ -508,11 +524,10 @@ __global__ void __launch_bounds__(256) back_affine_kernel(const MatchLaunch L, c
     const int i = e / N, j = e % N;
     const float gm = tap[i] * tap[j] * (gmp[e] - mean_term);
     const float di = i - c, dj = j - c;
-    const float Y = my + c + th[0] * di + th[1] * dj + th[2];
-    const float X = mx + c + th[3] * di + th[4] * dj + th[5];
-    const int y0 = min(static_cast<int>(floorf(Y)), L.mov_h - 2);
-    const int x0 = min(static_cast<int>(floorf(X)), L.mov_w - 2);
-    const float fy = Y - y0, fx = X - x0;
+    int y0, x0;
+    float fy, fx;
+    warp_tap(cy, th[0] * di + th[1] * dj + th[2], L.mov_h - 2, y0, fy);
+    warp_tap(cx, th[3] * di + th[4] * dj + th[5], L.mov_w - 2, x0, fx);
     const TIn* p = mov + static_cast<long long>(y0) * L.mov_pitch + x0;
     const float s00 = load_px<TIn>(p), s01 = load_px<TIn>(p + 1);
     const float s10 = load_px<TIn>(p + L.mov_pitch), s11 = load_px<TIn>(p + L.mov_pitch + 1);
