@@ -12,13 +12,16 @@ and on properties that hold at any size.
   64 distinct shifted-patch pairs repeated 128 times: every repetition must
   give the same result, and samples from every workspace slice match the
   oracle.
+- Models and pyramid: a 9-section 4096^2 uint8 stack (one section marked
+  damaged), Z models (k = 4) bit-exact in full, 2x / 4x levels of the batch
+  bit-exact on two sections.
 """
 import numpy as np
 import pytest
 import torch
 
 import synth
-from oracle import swim
+from oracle import remod, swim
 from parity import compare, oracle_window
 
 pytestmark = pytest.mark.gpu
@@ -123,3 +126,22 @@ def test_precision_full_size_tiled(n, precision):
     for i in [5, 2048 + 17, 4096 + 40, 6144 + 63]:  # one sample in each slice of 2048
         o, tied = oracle_window(mov[i].astype(np.float64), ref[i].astype(np.float64), olv)
         compare(g, i, o, tied, n, f"full-size {precision} n={n}")
+
+
+def test_models_and_pyramid_full_size():
+    size, Z, k = 4096, 9, 4
+    a, _ = synth.em_section_pair(size)
+    rng = np.random.default_rng(90)
+    stack = np.stack([np.clip(np.roll(a, (z, -z), (0, 1)).astype(np.int16)
+                              + rng.integers(-6, 7, a.shape, dtype=np.int16), 0, 255).astype(np.uint8)
+                      for z in range(Z)])
+    valid = np.ones(Z, bool)
+    valid[6] = False
+    ts = T(stack)
+    model = swift.zmodel(ts, k, valid=T(valid.astype(np.uint8))).cpu().numpy()
+    np.testing.assert_array_equal(model, remod.zmodel(stack, k, valid))
+    for f in (2, 4):
+        got = swift.downsample(ts, f).cpu().numpy()
+        assert got.shape == (Z, size // f, size // f)
+        for z in (0, 6):
+            np.testing.assert_array_equal(got[z], remod.downsample(stack[z], f))
