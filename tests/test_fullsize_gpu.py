@@ -15,13 +15,17 @@ and on properties that hold at any size.
 - Models and pyramid: a 9-section 4096^2 uint8 stack (one section marked
   damaged), Z models (k = 4) bit-exact in full, 2x / 4x levels of the batch
   bit-exact on two sections.
+- Rendering: the 512-triangle mesh (cell 256, band 256) fitted to the SNR-
+  weighted correspondences of the 961-window grid, and the 4096^2 render of
+  the moving section: the fits against the FP64 oracle, 16 sampled rows of
+  the render against the oracle's.
 """
 import numpy as np
 import pytest
 import torch
 
 import synth
-from oracle import remod, swim
+from oracle import mir, remod, swim
 from parity import compare, oracle_window
 
 pytestmark = pytest.mark.gpu
@@ -145,3 +149,32 @@ def test_models_and_pyramid_full_size():
         assert got.shape == (Z, size // f, size // f)
         for z in (0, 6):
             np.testing.assert_array_equal(got[z], remod.downsample(stack[z], f))
+
+
+def test_rendering_full_size():
+    size, n, stride, cell = 4096, 256, 128, 256
+    a, b = synth.em_section_pair(size)
+    org = synth.grid_origins(size, n, stride)
+    da, db, dorg = T(a), T(b), T(org)
+    plan = swift.Plan([swift.Level(n, 0.65, "hann", 1.0, 3.0)], dtype="u8", max_windows=len(org))
+    res = plan.match(da, db, dorg, dorg)
+    q, p, w = swift.correspondences(res, dorg, dorg, n, min_snr=5.0)
+    mesh = swift.Mesh(0, 0, cell, size // cell, size // cell)
+    mesh_o = mir.Mesh(0, 0, cell, size // cell, size // cell)
+    th, st = swift.mesh_fit(q, p, w, mesh, cell)
+    out = swift.render(db, th, mesh, size, size, fill=0.0).cpu().numpy()
+    th, st = th.cpu().numpy(), st.cpu().numpy()
+    qn, pn, wn = q.cpu().numpy(), p.cpu().numpy(), w.cpu().numpy()
+    ot, ost = mir.mesh_fit(qn, pn, wn, mesh_o, cell)
+    np.testing.assert_array_equal(st, ost)
+    np.testing.assert_allclose(th, ot, rtol=1e-9, atol=1e-7)
+    rows = np.sort(np.random.default_rng(4096).choice(size, 16, replace=False))
+    ref = mir.render(b, th, mesh_o, size, size, 0.0, rows=rows)
+    Y, X = np.meshgrid(rows, np.arange(size), indexing="ij")
+    t6 = th[mesh_o.locate(Y, X)]
+    py = t6[..., 0] * Y + t6[..., 1] * X + t6[..., 2]
+    px = t6[..., 3] * Y + t6[..., 4] * X + t6[..., 5]
+    eps = 1e-3  # sample points this close to the source border may fall on either side
+    amb = (np.abs(py) < eps) | (np.abs(px) < eps) | (np.abs(py - (size - 1)) < eps) | (np.abs(px - (size - 1)) < eps)
+    assert (~amb).mean() > 0.99
+    assert np.abs(out[rows] - ref)[~amb].max() <= 0.05
