@@ -13,14 +13,19 @@
  *
  * Conventions shared by every entry point
  *   - All image, origin, level, affine and result arrays are DEVICE pointers
- *     owned by the caller.  A plan owns only its own small tables.
+ *     owned by the caller.  A plan owns only its tables and its workspace.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are stream-ordered and do not synchronise the host.
  *   - Argument errors are detected on the host before any launch and return a
  *     status other than SWIFT_OK with nothing written.  Launch failures return
  *     SWIFT_ERR_CUDA.  Per-window data problems are reported in
  *     swift_result.status, never as a call error.
- *   - A plan may be used by one stream at a time.  No entry point throws.
+ *   - The calls of one plan share its workspace, so they are ordered among
+ *     themselves on the device: a call made on a stream other than the
+ *     plan's previous call first makes its stream wait for that call's work
+ *     (an event the plan records after every call).  Calls captured into a
+ *     CUDA graph are not ordered this way; swift_plan_replay orders the
+ *     replays.  A plan is not thread-safe.  No entry point throws.
  */
 #ifndef SWIFT_H_
 #define SWIFT_H_

@@ -76,6 +76,11 @@ struct swift_plan_s {
   // one captured forward call (swift_plan_capture / swift_plan_replay)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // every call of the plan shares its workspace: an event recorded after each
+  // call, which a call arriving on another stream waits for first
+  cudaEvent_t order_ev = nullptr;
+  cudaStream_t order_stream = nullptr;
+  bool order_used = false;
 };
 
 namespace {
@@ -112,6 +117,7 @@ static swift_status release(swift_plan p) {
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->gw_acc) cudaFree(p->gw_acc);
+  if (p->order_ev) cudaEventDestroy(p->order_ev);
   if (cur != p->device) cudaSetDevice(cur);
   delete p;
   return SWIFT_OK;
@@ -144,6 +150,12 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
   p->max_windows = max_windows;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
+    return SWIFT_ERR_CUDA;
+  }
+  if (cudaEventCreateWithFlags(&p->order_ev, cudaEventDisableTiming) != cudaSuccess) {
+    p->order_ev = nullptr;
+    release(p);
+    cudaGetLastError();
     return SWIFT_ERR_CUDA;
   }
   double a[512];
@@ -304,6 +316,47 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
 static swift_status check_warp_batch(swift_plan plan, const swift_batch* batch);
 static swift_status warp_forward(swift_plan plan, const swift_batch* batch, swift_result* out, cudaStream_t st);
 
+// Calls of one plan share its workspace.  A call that arrives on a stream
+// other than the previous call's first makes its stream wait, on the device,
+// for the previous call's work; every call then records the plan's event.
+// Work being captured into a graph is left out (a capturing stream may not
+// wait on an event recorded outside the capture); swift_plan_replay orders the
+// graph's launches instead.
+static swift_status order_begin(swift_plan p, cudaStream_t st, bool* captured) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return SWIFT_ERR_CUDA;
+  }
+  *captured = cs != cudaStreamCaptureStatusNone;
+  if (*captured || !p->order_used || p->order_stream == st) return SWIFT_OK;
+  if (cudaStreamWaitEvent(st, p->order_ev, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return SWIFT_ERR_CUDA;
+  }
+  return SWIFT_OK;
+}
+
+static void order_end(swift_plan p, cudaStream_t st, bool captured) {
+  if (captured) return;
+  if (cudaEventRecord(p->order_ev, st) == cudaSuccess) {
+    p->order_stream = st;
+    p->order_used = true;
+  }
+}
+
+// the launches of one validated forward call
+static swift_status match_launches(swift_plan plan, const swift_batch* batch, swift_result* out, cudaStream_t st) {
+  if (batch->affine) return warp_forward(plan, batch, out, st);
+  const int used_levels = batch->level ? plan->n_levels : 1;
+  for (int l = 0; l < used_levels; ++l) {
+    const swift_status e = run_level(plan, batch, l, out, st);
+    if (e != SWIFT_OK) return e;
+  }
+  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
+  return SWIFT_OK;
+}
+
 extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_result* out,
                                           void* stream) {
   if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
@@ -322,18 +375,17 @@ extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* ba
   }
   // report (and clear) an asynchronous failure left by earlier work
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (batch->affine) {
     const swift_status e = check_warp_batch(plan, batch);
     if (e != SWIFT_OK) return e;
-    return warp_forward(plan, batch, out, st);
   }
-  for (int l = 0; l < used_levels; ++l) {
-    const swift_status e = run_level(plan, batch, l, out, st);
-    if (e != SWIFT_OK) return e;
-  }
-  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
-  return SWIFT_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool captured = false;
+  const swift_status oe = order_begin(plan, st, &captured);
+  if (oe != SWIFT_OK) return oe;
+  const swift_status e = match_launches(plan, batch, out, st);
+  order_end(plan, st, captured);
+  return e;
 }
 
 // Launch description of level l (shared by the warp and backward paths).
@@ -435,6 +487,9 @@ static swift_status warp_forward(swift_plan plan, const swift_batch* batch, swif
   return SWIFT_OK;
 }
 
+static swift_status backward_launches(swift_plan plan, const swift_batch* batch, const float* grad_peak,
+                                      const float* grad_snr, float* grad_affine, float* grad_w, cudaStream_t st);
+
 extern "C" swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, const float* grad_peak,
                                              const float* grad_snr, float* grad_affine, float* grad_w,
                                              void* stream) {
@@ -446,6 +501,17 @@ extern "C" swift_status swift_match_backward(swift_plan plan, const swift_batch*
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   if ((e = ensure_bwork(plan)) != SWIFT_OK) return e;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool captured = false;
+  if ((e = order_begin(plan, st, &captured)) != SWIFT_OK) return e;
+  e = backward_launches(plan, batch, grad_peak, grad_snr, grad_affine, grad_w, st);
+  order_end(plan, st, captured);
+  return e;
+}
+
+// the launches of one validated backward call
+static swift_status backward_launches(swift_plan plan, const swift_batch* batch, const float* grad_peak,
+                                      const float* grad_snr, float* grad_affine, float* grad_w, cudaStream_t st) {
+  const long long B = batch->n_windows;
   if (cudaMemsetAsync(plan->gw_acc, 0, sizeof(double) * kMaxLevels, st) != cudaSuccess) return SWIFT_ERR_CUDA;
   const int used = batch->level ? plan->n_levels : 1;
   for (int l = 0; l < used && B > 0; ++l) {
@@ -556,7 +622,13 @@ extern "C" swift_status swift_plan_capture(swift_plan plan, const swift_batch* b
 
 extern "C" swift_status swift_plan_replay(swift_plan plan, void* stream) {
   if (!plan || !plan->graph_exec) return SWIFT_ERR_INVALID_ARG;
-  if (cudaGraphLaunch(plan->graph_exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool captured = false;
+  const swift_status oe = order_begin(plan, st, &captured);
+  if (oe != SWIFT_OK) return oe;
+  const cudaError_t ge = cudaGraphLaunch(plan->graph_exec, st);
+  order_end(plan, st, captured);
+  if (ge != cudaSuccess) {
     cudaGetLastError();
     return SWIFT_ERR_CUDA;
   }

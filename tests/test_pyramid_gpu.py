@@ -138,3 +138,31 @@ def test_four_sizes_64_to_512_in_one_call_and_one_graph():
         for i in idx:
             o, tied = oracle_window(swim.gather(imgs_b[l], org[i], lv.n), swim.gather(imgs_a[l], org[i], lv.n), olv)
             compare(g, i, o, tied, lv.n, f"four sizes level {l}")
+
+
+def test_calls_on_two_streams_are_ordered_by_the_plan(pyramid):
+    """One plan called on two non-blocking streams, each call issued while
+    the other stream's call may still run, and graph replays alternating
+    with direct calls: the calls share the plan's workspace, so each waits
+    for the plan's previous call, and every result equals a lone call's."""
+    P = pyramid
+    args = (P["ta"], P["tb"], P["to"], P["to"])
+    plan = swift.Plan(LEVELS, dtype="u8", max_windows=len(P["org"]))
+    for l in range(len(LEVELS)):
+        plan.set_schedule(l, "stream")
+    want = swift.decode(plan.match(*args, level=P["tl"]))
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.full((len(P["org"]), 8), -1, dtype=torch.int32, device=DEV) for _ in range(12)]
+    torch.cuda.synchronize()
+    for i in range(8):
+        plan.match(*args, level=P["tl"], out=outs[i], stream=s1 if i % 2 == 0 else s2)
+    with torch.cuda.stream(s1):
+        g_out = plan.capture(*args, level=P["tl"], stream=s1)
+    for i in range(8, 12):
+        plan.replay(s2 if i % 2 == 0 else s1)
+        plan.match(*args, level=P["tl"], out=outs[i], stream=s1 if i % 2 == 0 else s2)
+    torch.cuda.synchronize()
+    for out in outs + [g_out]:
+        got = swift.decode(out)
+        for k in want:
+            assert (got[k] == want[k]).all(), k
