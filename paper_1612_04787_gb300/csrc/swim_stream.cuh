@@ -217,12 +217,75 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
 // ---------------------------------------------------------------------------
 // K1: row transforms of z = m' + i r'
 // ---------------------------------------------------------------------------
+// 16 x 16 byte transpose within each half-warp.  On entry lane L (its lane
+// index mod 16) holds bytes t = 0..15 of chunk L (byte t in w[t / 4] at bit
+// 8 (t % 4)); on exit it holds byte L of every chunk, chunk m as byte m.
+// Each of the four stages swaps one bit of the lane index with the same bit
+// of the byte index: lanes L and L ^ d trade the half of their bytes whose
+// bit differs from their own lane bit (two words per shuffle).
+__device__ __forceinline__ void transpose16_u8(uint32_t (&w)[4], int L) {
+  {  // lane bit 3 <-> byte bit 3 (word pairs {0,1} / {2,3})
+    const bool hi = (L & 8) != 0;
+    uint32_t a = hi ? w[0] : w[2], b = hi ? w[1] : w[3];
+    a = __shfl_xor_sync(0xffffffffu, a, 8);
+    b = __shfl_xor_sync(0xffffffffu, b, 8);
+    if (hi) {
+      w[0] = a;
+      w[1] = b;
+    } else {
+      w[2] = a;
+      w[3] = b;
+    }
+  }
+  {  // lane bit 2 <-> byte bit 2 (words {0,2} / {1,3})
+    const bool hi = (L & 4) != 0;
+    uint32_t a = hi ? w[0] : w[1], b = hi ? w[2] : w[3];
+    a = __shfl_xor_sync(0xffffffffu, a, 4);
+    b = __shfl_xor_sync(0xffffffffu, b, 4);
+    if (hi) {
+      w[0] = a;
+      w[2] = b;
+    } else {
+      w[1] = a;
+      w[3] = b;
+    }
+  }
+  {  // lane bit 1 <-> byte bit 1 (16-bit halves of each word)
+    const bool hi = (L & 2) != 0;
+    const uint32_t give = hi ? 0x5410u : 0x7632u;
+    uint32_t a = __byte_perm(w[0], w[1], give), b = __byte_perm(w[2], w[3], give);
+    a = __shfl_xor_sync(0xffffffffu, a, 2);
+    b = __shfl_xor_sync(0xffffffffu, b, 2);
+    const uint32_t s0 = hi ? 0x3254u : 0x5410u, s1 = hi ? 0x3276u : 0x7610u;
+    w[0] = __byte_perm(w[0], a, s0);
+    w[1] = __byte_perm(w[1], a, s1);
+    w[2] = __byte_perm(w[2], b, s0);
+    w[3] = __byte_perm(w[3], b, s1);
+  }
+  {  // lane bit 0 <-> byte bit 0 (odd / even bytes of each word)
+    const bool hi = (L & 1) != 0;
+    const uint32_t give = hi ? 0x6420u : 0x7531u;
+    uint32_t a = __byte_perm(w[0], w[1], give), b = __byte_perm(w[2], w[3], give);
+    a = __shfl_xor_sync(0xffffffffu, a, 1);
+    b = __shfl_xor_sync(0xffffffffu, b, 1);
+    const uint32_t s0 = hi ? 0x3514u : 0x5240u, s1 = hi ? 0x3716u : 0x7260u;
+    w[0] = __byte_perm(w[0], a, s0);
+    w[1] = __byte_perm(w[1], a, s1);
+    w[2] = __byte_perm(w[2], b, s0);
+    w[3] = __byte_perm(w[3], b, s1);
+  }
+}
+
 template <int N, typename TIn>
 __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, const StreamWork W) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, RB = G::RB, RS = G::RS, T = G::T;
   constexpr int KB = (RB * R1 + T - 1) / T;
   constexpr int MS = G::template stage_stride<TIn>();
+  constexpr int TS = R1 + 4;  // row stride of the transposed column taper (16-byte rows, no bank conflicts)
+  // uint8 windows of 256 x 256: pass A takes its pixels from the thread's own
+  // 16-byte loads through a half-warp byte transpose instead of a staged copy
+  constexpr bool kShfl = N == 256 && sizeof(TIn) == 1;
   const long long s = blockIdx.x / (N / RB);
   const int rb = blockIdx.x % (N / RB);
   const long long b = W.b0 + s;
@@ -233,14 +296,17 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [RB][RS]
   float2* twid = slab + RB * RS;
   float* tap = reinterpret_cast<float*>(twid + N);
+  float* tapT = tap + N;  // [R2][TS]: tapT[j][m] = tap[j + R2 m]
   // raw rows: uint8/float32 moving and reference; the reference of a K-section
   // model (or unaligned rows) is staged as float in rfstage, which aliases the slab
-  TIn* mstage = reinterpret_cast<TIn*>(tap + N);  // [RB][MS]
+  TIn* mstage = reinterpret_cast<TIn*>(tapT + R2 * TS);  // [RB][MS]
   TIn* rstage = mstage + RB * MS;
   float* rfstage = reinterpret_cast<float*>(slab);
   for (int i = tid; i < N; i += T) {
     twid[i] = L.twiddle[i];
-    tap[i] = L.taper[i];
+    const float t = L.taper[i];
+    tap[i] = t;
+    tapT[(i % R2) * TS + i / R2] = t;
   }
   const TIn* mbase;
   const TIn* rbase;
@@ -269,8 +335,16 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   const bool vec = L.ref_count == 1 && ((reinterpret_cast<uintptr_t>(mbase) | reinterpret_cast<uintptr_t>(rbase) |
                                          static_cast<uintptr_t>(mpitch * sizeof(TIn)) |
                                          static_cast<uintptr_t>(rpitch * sizeof(TIn))) & 15) == 0;
+  uint32_t wm[4] = {0u, 0u, 0u, 0u}, wr[4] = {0u, 0u, 0u, 0u};  // kShfl: bytes 16 L .. 16 L + 15 of a row
   if (vec) {
-    if constexpr (sizeof(TIn) == 4) {
+    if constexpr (kShfl) {
+      static_assert(RB * N / 16 == T && R2 == 16, "one 16-byte vector per thread and window");
+      const int r = tid / 16, x0 = (tid % 16) * 16;
+      const uint4 a = __ldg(reinterpret_cast<const uint4*>(mbase + r * mpitch + x0));
+      const uint4 c = __ldg(reinterpret_cast<const uint4*>(rbase + r * rpitch + x0));
+      wm[0] = a.x, wm[1] = a.y, wm[2] = a.z, wm[3] = a.w;
+      wr[0] = c.x, wr[1] = c.y, wr[2] = c.z, wr[3] = c.w;
+    } else if constexpr (sizeof(TIn) == 4) {
       __shared__ __align__(8) unsigned long long stage_bar;
       const uint32_t mbar = smem_addr(&stage_bar);
       constexpr uint32_t kRowBytes = N * sizeof(TIn);
@@ -335,19 +409,36 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   const int line = tid / R2, j = tid % R2;
   const int y = rb * RB + line;
   float mv[R1], rv[R1];
+  if (kShfl && vec) {
+    // lane j of the half-warp of row `line` receives x = j + 16 m, m = 0..15
+    transpose16_u8(wm, j);
+    transpose16_u8(wr, j);
 #pragma unroll
-  for (int m = 0; m < R1; ++m) {
-    const int e = line * MS + j + R2 * m;
-    mv[m] = static_cast<float>(mstage[e]);
-    rv[m] = vec ? static_cast<float>(rstage[e]) : rfstage[e];
+    for (int m = 0; m < R1; ++m) {
+      mv[m] = static_cast<float>((wm[m >> 2] >> (8 * (m & 3))) & 0xffu);
+      rv[m] = static_cast<float>((wr[m >> 2] >> (8 * (m & 3))) & 0xffu);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+      const int e = line * MS + j + R2 * m;
+      mv[m] = static_cast<float>(mstage[e]);
+      rv[m] = vec ? static_cast<float>(rstage[e]) : rfstage[e];
+    }
   }
   if (!vec) __syncthreads();  // rfstage aliases the slab written below
   {
     const float ay = tap[y];
+    float tx[R1];
+#pragma unroll
+    for (int q = 0; q < R1 / 4; ++q) {
+      const float4 t4 = reinterpret_cast<const float4*>(tapT + j * TS)[q];
+      tx[4 * q] = t4.x, tx[4 * q + 1] = t4.y, tx[4 * q + 2] = t4.z, tx[4 * q + 3] = t4.w;
+    }
     float2 v[R1];
 #pragma unroll
     for (int m = 0; m < R1; ++m) {
-      const float a = ay * tap[j + R2 * m];
+      const float a = ay * tx[m];
       v[m] = make_float2(a * (mv[m] - st.x), a * (rv[m] - st.y));
     }
     dft<R1, -1>(v);
@@ -735,7 +826,7 @@ __global__ void __launch_bounds__(256) stream_final_kernel(const MatchLaunch L, 
 template <int N, typename TIn>
 constexpr size_t rows_smem() {
   using G = StreamGeom<N>;
-  return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * N +
+  return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * (N + G::R2 * (G::R1 + 4)) +
          2 * sizeof(TIn) * G::RB * G::template stage_stride<TIn>();
 }
 template <int N>
