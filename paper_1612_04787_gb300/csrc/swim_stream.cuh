@@ -485,8 +485,12 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
   if (stat_status(W.stats[s]) != SWIFT_WIN_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [ky][lc], row stride LS
-  float2* twid = slab + N * LS;
-  for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
+  // twiddles transposed, [k1][n2] with rows of R2 + 2 (16-byte multiples, two
+  // CTA-uniform rows per warp on different banks): a thread of passes B / B'
+  // reads its R2 twiddles as R2 / 2 16-byte pairs
+  constexpr int TW = R2 + 2;
+  float2* twT = slab + N * LS;
+  for (int i = tid; i < N; i += T) twT[(i % R1) * TW + i / R1] = L.twiddle[i];
   // column pass A (rows j + R2 m) straight from Zr: consecutive threads take
   // consecutive lines, i.e. contiguous kx runs of a row (coalesced)
   const float2* zr = W.zr + s * N * N;
@@ -513,9 +517,13 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
     const int k1 = task / LINES, lc = task % LINES;
     float2 v[R2];
 #pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) {
-      const float2 x = slab[(R2 * k1 + n2) * LS + lc];
-      v[n2] = n2 == 0 ? x : cmul(x, twid[n2 * R1 + k1]);
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = slab[(R2 * k1 + n2) * LS + lc];
+    const float4* tw4 = reinterpret_cast<const float4*>(twT + k1 * TW);
+#pragma unroll
+    for (int q = 0; q < R2 / 2; ++q) {
+      const float4 t = tw4[q];
+      if (q > 0) v[2 * q] = cmul(v[2 * q], make_float2(t.x, t.y));
+      v[2 * q + 1] = cmul(v[2 * q + 1], make_float2(t.z, t.w));
     }
     dft<R2, -1>(v);
 #pragma unroll
@@ -587,8 +595,13 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) v[k2] = slab[(R2 * k1 + k2) * LS + lc];
     dft<R2, +1>(v);
+    const float4* tw4 = reinterpret_cast<const float4*>(twT + k1 * TW);
 #pragma unroll
-    for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(v[n2], twid[n2 * R1 + k1]);
+    for (int q = 0; q < R2 / 2; ++q) {
+      const float4 t = tw4[q];
+      if (q > 0) v[2 * q] = cmulc(v[2 * q], make_float2(t.x, t.y));
+      v[2 * q + 1] = cmulc(v[2 * q + 1], make_float2(t.z, t.w));
+    }
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) slab[(R2 * k1 + n2) * LS + lc] = v[n2];
   }
@@ -832,7 +845,7 @@ constexpr size_t rows_smem() {
 template <int N>
 constexpr size_t cols_smem() {
   using G = StreamGeom<N>;
-  return sizeof(float2) * (N * (2 * G::CB + 8) + N);
+  return sizeof(float2) * (N * (2 * G::CB + 8) + G::R1 * (G::R2 + 2));
 }
 template <int N>
 constexpr size_t irows_smem() {
