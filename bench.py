@@ -1019,8 +1019,12 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
-KERNEL_NAMES = {"stats": "stream_stats_kernel", "rows": "stream_rows_kernel", "cols": "stream_cols_kernel",
-                "irows": "stream_irows_kernel", "final": "stream_final_kernel", "fused": "swim_forward_kernel"}
+def kernel_names(n: int) -> dict:
+    """Kernel of each streaming slot of the FP32 schedule at window size n
+    (column pairs up to 256, per-column kernel at 512)."""
+    return {"stats": "stream_stats_kernel", "rows": "stream_rows_kernel",
+            "cols": "stream_cpair_kernel" if n <= 256 else "stream_cols_kernel",
+            "irows": "stream_irows_kernel", "final": "stream_peak_kernel", "fused": "swim_forward_kernel"}
 TC_KERNEL_NAMES = {"stats": "stream_stats_kernel", "rows": "tcf_rows_kernel", "cols": "tcf_cols_kernel",
                    "irows": "tcf_irows_kernel", "final": "stream_final_kernel"}
 
@@ -1156,7 +1160,7 @@ def main():
         achieved = per_window * windows_per_launch / (dom_ms / 1e3) / 1e12
         tot = sum(x[0] for x in kt.values())
         shares = {k: round(v[0] / tot, 4) for k, v in kt.items()}
-        dom_name = (TC_KERNEL_NAMES if tensor else KERNEL_NAMES)[dom]
+        dom_name = (TC_KERNEL_NAMES if tensor else kernel_names(W.dominant_n))[dom]
     else:
         dom_name, achieved, shares, windows_per_launch = "pipeline (graph replay)", step_tflops, None, W.windows
     traffic = recorded_traffic(f"{dom_name}<{W.dominant_n}>", windows_per_launch)

@@ -198,9 +198,10 @@ swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_
  * framework.  No plan is needed and nothing is allocated: the scratch this
  * path needs (window statistics, row spectra, whitened inverse-column data,
  * the match response) lives in one 24 MiB file-scope device array that every
- * GPU which loads the library holds until the process exits.  The taper and
- * twiddle tables are built on the host for `level` and copied into that array
- * on `stream` at every call.  The paper has no counterpart: this is a
+ * GPU which loads the library holds until the process exits.  At every call
+ * a small kernel on `stream` computes the taper and twiddle tables of `level`
+ * straight into that array (no host buffer is read).  The paper has no
+ * counterpart: this is a
  * deployment variant of swift_match_batch for a single level (batch->level
  * must be NULL); it runs the same streaming kernels and gives the same
  * results.
@@ -211,8 +212,11 @@ swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_
  * batches return SWIFT_ERR_CAPACITY before any work is queued; split them.
  *
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before capturing any stream into a CUDA graph.
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before capturing any stream into a
+ * CUDA graph.  The kept address belongs to the device's context: after
+ * cudaDeviceReset on that device, do not call this entry point again in the
+ * same process.
  *
  * Sharing: all calls on a device use the same array and it keeps the last
  * call's contents (nothing in it has to start at zero).  Calls that overlap
@@ -287,6 +291,15 @@ swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
  * uint8 windows, the fused schedule and the tensor-core forms do not use
  * this staging and are unaffected. */
 swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enable);
+
+/* Test hook for the window guard (not for production use).  While enabled,
+ * the statistics kernel of the FP32 streaming schedule reports windows of
+ * other levels as OK without reading them -- the state a raced or stale
+ * workspace could leave.  The row kernels re-check every window's level and
+ * bounds from the batch's own arrays (swift_window_check) before turning an
+ * origin into an address, so such a window is still skipped and its result
+ * record is left as it was. */
+swift_status swift_plan_set_test_stale_status(swift_plan plan, int32_t enable);
 swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, int32_t* launches);
 
 /* ------------------------------------------------------------------------
@@ -411,6 +424,16 @@ swift_status swift_zmodel(const uint8_t* stack, int64_t stride, int32_t n_sectio
 swift_status swift_plan_set_whitening(swift_plan plan, int32_t level, float w);
 
 /* Human-readable name of a status code (static string). */
+/* The window guard that every kernel applies before it turns an origin into
+ * an address: a window of side n whose level index is `level` belongs to a
+ * launch of level `want_level`, and its reference window at ref_origin (y, x)
+ * and moving window at mov_origin (y, x) lie inside images of ref_h x ref_w
+ * and mov_h x mov_w pixels.  Host function (no GPU needed).
+ * Returns SWIFT_WIN_OK (0), SWIFT_WIN_OUT_OF_BOUNDS (1), or -1 for a window
+ * of another level (skipped: no result is written for it by that launch). */
+int32_t swift_window_check(int32_t n, int32_t level, int32_t want_level, const int32_t* ref_origin,
+                           const int32_t* mov_origin, int32_t ref_h, int32_t ref_w, int32_t mov_h, int32_t mov_w);
+
 const char* swift_status_string(swift_status s);
 
 /* Library version string, e.g. "swift-gb300 0.1 sm_103a". */

@@ -176,6 +176,12 @@ class Plan:
         so its bounded wait runs out and windows report status 4 (timeout)."""
         check(lib.swift_plan_set_test_stall(self._h, 1 if enable else 0), "swift_plan_set_test_stall")
 
+    def set_test_stale_status(self, enable: bool):
+        """Test hook: the statistics kernel reports windows of other levels as
+        OK without reading them; the row kernels' own guard must skip them."""
+        check(lib.swift_plan_set_test_stale_status(self._h, 1 if enable else 0),
+              "swift_plan_set_test_stale_status")
+
     def set_timing(self, enable: bool):
         """Record CUDA events around every kernel of later forward calls."""
         check(lib.swift_plan_set_timing(self._h, 1 if enable else 0), "swift_plan_set_timing")
@@ -266,6 +272,15 @@ def match_warped(plan: Plan, ref, mov, ref_origin, mov_origin, affine, w, level=
     ``w`` through the library's backward kernels.
     """
     return _MatchFn.apply(affine, w, plan, ref, mov, ref_origin, mov_origin, level)
+
+
+def window_check(n: int, level: int, want_level: int, ref_origin, mov_origin, ref_shape, mov_shape) -> int:
+    """The kernels' window guard on the host: 0 (readable), 1 (out of bounds)
+    or -1 (a window of another level)."""
+    ro = (C.c_int32 * 2)(*[int(v) for v in ref_origin])
+    mo = (C.c_int32 * 2)(*[int(v) for v in mov_origin])
+    return int(lib.swift_window_check(int(n), int(level), int(want_level), ro, mo, int(ref_shape[0]),
+                                      int(ref_shape[1]), int(mov_shape[0]), int(mov_shape[1])))
 
 
 def decode(res) -> dict:

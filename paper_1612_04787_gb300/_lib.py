@@ -41,6 +41,8 @@ EXPORTS = (
     "swift_plan_replay",
     "swift_plan_set_timing",
     "swift_plan_set_test_stall",
+    "swift_plan_set_test_stale_status",
+    "swift_window_check",
     "swift_plan_timings",
     "swift_status_string",
     "swift_version",
@@ -120,6 +122,11 @@ def _load():
     lib.swift_plan_set_timing.restype = C.c_int
     lib.swift_plan_set_test_stall.argtypes = [C.c_void_p, C.c_int32]
     lib.swift_plan_set_test_stall.restype = C.c_int
+    lib.swift_plan_set_test_stale_status.argtypes = [C.c_void_p, C.c_int32]
+    lib.swift_plan_set_test_stale_status.restype = C.c_int
+    lib.swift_window_check.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    lib.swift_window_check.restype = C.c_int32
     lib.swift_plan_timings.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
     lib.swift_plan_timings.restype = C.c_int
     lib.swift_status_string.argtypes = [C.c_int]

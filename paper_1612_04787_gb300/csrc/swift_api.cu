@@ -24,24 +24,9 @@ int size_slot(int n) {
 // window sizes with a fused (cluster) kernel; 512 x 512 windows always stream
 bool has_fused(int n) { return n <= 256; }
 
-// 1D taper in FP64 (Sec. III: cosine taper).  Periodic convention: Hann is
-// a[k] = (1 - cos(2 pi k / n)) / 2; Tukey(alpha) has raised-cosine ramps of
-// alpha*n/2 samples at each edge and is 1 in between.
+// 1D taper of a level in FP64 (swift::taper_value)
 void taper_table(int n, int apod, double alpha, double* a) {
-  if (apod == SWIFT_APOD_NONE) {
-    for (int k = 0; k < n; ++k) a[k] = 1.0;
-    return;
-  }
-  if (apod == SWIFT_APOD_HANN) alpha = 1.0;
-  const double ramp = alpha * n / 2.0;
-  for (int k = 0; k < n; ++k) {
-    double v = 1.0;
-    if (k < ramp)
-      v = 0.5 * (1.0 - cos(M_PI * k / ramp));
-    else if (k > n - ramp)
-      v = 0.5 * (1.0 - cos(M_PI * (n - k) / ramp));
-    a[k] = v;
-  }
+  for (int k = 0; k < n; ++k) a[k] = swift::taper_value(n, apod, alpha, k);
 }
 
 }  // namespace
@@ -69,6 +54,7 @@ struct swift_plan_s {
   // per-kernel timing (swift_plan_set_timing / swift_plan_timings): a ring
   // of event sets, one set per streaming slice or fused launch
   bool test_stall = false;  // swift_plan_set_test_stall
+  bool test_stale_ok = false;  // swift_plan_set_test_stale_status
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // [kTimingSets][6]
   int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch
@@ -181,12 +167,7 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
       int r1 = 0, r2 = 0;
       swift::stream_radices(n, &r1, &r2);
       float2 tw[512];
-      for (int m = 0; m < r2; ++m)
-        for (int j = 0; j < r1; ++j) {
-          const int e = (j * m) % n;
-          const double ang = -2.0 * M_PI * e / n;
-          tw[m * r1 + j] = make_float2(static_cast<float>(cos(ang)), static_cast<float>(sin(ang)));
-        }
+      for (int i = 0; i < r1 * r2; ++i) tw[i] = swift::twiddle_entry(n, r1, i);
       if (cudaMalloc(&p->twiddle[slot], sizeof(float2) * n) != cudaSuccess ||
           cudaMemcpy(p->twiddle[slot], tw, sizeof(float2) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
         release(p);
@@ -268,6 +249,7 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
   L.taper = plan->taper[l];
   L.twiddle = plan->twiddle[size_slot(lv.n)];
   L.stall_tx = plan->test_stall ? 16u : 0u;
+  L.stale_ok = plan->test_stale_ok ? 1 : 0;
   L.out = out;
   if (plan->prec != SWIFT_PREC_FP32) {
     const bool fp16 = plan->prec == SWIFT_PREC_FP16X2;
@@ -417,6 +399,7 @@ static swift::MatchLaunch level_launch(swift_plan plan, const swift_batch* batch
   L.taper = plan->taper[l];
   L.twiddle = plan->twiddle[size_slot(lv.n)];
   L.stall_tx = plan->test_stall ? 16u : 0u;
+  L.stale_ok = plan->test_stale_ok ? 1 : 0;
   L.out = out;
   L.pre_status = nullptr;
   return L;
@@ -639,6 +622,20 @@ extern "C" swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enabl
   if (!plan) return SWIFT_ERR_INVALID_ARG;
   plan->test_stall = enable != 0;
   return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_test_stale_status(swift_plan plan, int32_t enable) {
+  if (!plan) return SWIFT_ERR_INVALID_ARG;
+  plan->test_stale_ok = enable != 0;
+  return SWIFT_OK;
+}
+
+extern "C" int32_t swift_window_check(int32_t n, int32_t level, int32_t want_level, const int32_t* ref_origin,
+                                      const int32_t* mov_origin, int32_t ref_h, int32_t ref_w, int32_t mov_h,
+                                      int32_t mov_w) {
+  if (!ref_origin || !mov_origin || n < 1) return SWIFT_WIN_OUT_OF_BOUNDS;
+  return swift::window_check(n, level, want_level, ref_origin[0], ref_origin[1], mov_origin[0], mov_origin[1], ref_h,
+                             ref_w, mov_h, mov_w);
 }
 
 extern "C" swift_status swift_plan_set_timing(swift_plan plan, int32_t enable) {

@@ -7,6 +7,52 @@
 
 namespace swift {
 
+// ---------------------------------------------------------------------------
+// Window guard.  Window b of a launch may be read only when it belongs to the
+// launch's level and, in section mode, both n x n windows lie inside their
+// images.  Every kernel that turns an origin into an address evaluates this
+// itself from the level and origin arrays (a few integer compares per CTA), so
+// no status word in a shared workspace ever decides whether a read is made.
+// ---------------------------------------------------------------------------
+constexpr int kWindowOtherLevel = -1;  // window of another level: skipped, no result written
+
+__host__ __device__ inline bool window_inside(int n, int y, int x, int h, int w) {
+  return y >= 0 && x >= 0 && y <= h - n && x <= w - n;
+}
+
+// SWIFT_WIN_OK, SWIFT_WIN_OUT_OF_BOUNDS or kWindowOtherLevel
+__host__ __device__ inline int window_check(int n, int level, int want_level, int ry, int rx, int my, int mx,
+                                            int ref_h, int ref_w, int mov_h, int mov_w) {
+  if (level != want_level) return kWindowOtherLevel;
+  return window_inside(n, ry, rx, ref_h, ref_w) && window_inside(n, my, mx, mov_h, mov_w) ? SWIFT_WIN_OK
+                                                                                          : SWIFT_WIN_OUT_OF_BOUNDS;
+}
+
+// ---------------------------------------------------------------------------
+// Per-level tables, shared by the plan (built on the host) and the
+// allocation-free entry point (built on the device).
+// ---------------------------------------------------------------------------
+// 1D taper in FP64 (Sec. III: cosine taper).  Periodic convention: Hann is
+// a[k] = (1 - cos(2 pi k / n)) / 2; Tukey(alpha) has raised-cosine ramps of
+// alpha*n/2 samples at each edge and is 1 in between; NONE is 1.
+__host__ __device__ inline double taper_value(int n, int apod, double alpha, int k) {
+  if (apod == SWIFT_APOD_NONE) return 1.0;
+  if (apod == SWIFT_APOD_HANN) alpha = 1.0;
+  const double ramp = alpha * n / 2.0;
+  const double pi = 3.14159265358979323846;
+  if (k < ramp) return 0.5 * (1.0 - cos(pi * k / ramp));
+  if (k > n - ramp) return 0.5 * (1.0 - cos(pi * (n - k) / ramp));
+  return 1.0;
+}
+
+// Entry i of the streaming kernels' twiddle table, stored [m][j] (j < r1):
+// W_n^(j m) = exp(-2 pi i (j m mod n) / n), rounded to FP32.
+__host__ __device__ inline float2 twiddle_entry(int n, int r1, int i) {
+  const int j = i % r1, m = i / r1;
+  const double ang = -2.0 * 3.14159265358979323846 * ((j * m) % n) / n;
+  return make_float2(static_cast<float>(cos(ang)), static_cast<float>(sin(ang)));
+}
+
 // Everything one forward launch needs, passed by value as the kernel argument.
 struct MatchLaunch {
   const void* ref;  // reference image (or first of ref_count sections)
@@ -29,6 +75,7 @@ struct MatchLaunch {
   swift_result* out;                 // [B]
   const int* pre_status = nullptr;   // [slice] status decided before the statistics (or null)
   unsigned int stall_tx = 0;         // test hook: bytes the float row staging waits for that never arrive
+  int stale_ok = 0;                  // test hook: statistics report OK for windows of other levels
 };
 
 // Workspace of the streaming forward path for one slice of windows.

@@ -45,6 +45,25 @@ __device__ __forceinline__ void warp_tap(int base, float local, int last_pair, i
   f = (local - fl) + static_cast<float>(t - t0);
 }
 
+// Whether every sample of the warped moving window lies in the image: the
+// four corners of the window, mapped by the affine about its centre (cy, cx),
+// within [0, h - 1] x [0, w - 1].  Part of the window guard of the kernels
+// that read the warped window (preparation and the affine adjoint).
+template <int N>
+__device__ __forceinline__ bool warped_inside(const float (&th)[6], int cy, int cx, int h, int w) {
+  const float c = 0.5f * N;
+  bool ok = true;
+#pragma unroll
+  for (int corner = 0; corner < 4; ++corner) {
+    const float di = (corner & 1 ? N - 1 : 0) - c, dj = (corner & 2 ? N - 1 : 0) - c;
+    const float ly = th[0] * di + th[1] * dj + th[2];
+    const float lx = th[3] * di + th[4] * dj + th[5];
+    ok = ok && ly >= static_cast<float>(-cy) && lx >= static_cast<float>(-cx) && ly <= static_cast<float>(h - 1 - cy) &&
+         lx <= static_cast<float>(w - 1 - cx);
+  }
+  return ok;
+}
+
 template <int N, typename TIn>
 __global__ void __launch_bounds__(256) prep_kernel(const MatchLaunch L, const BackLaunch K, const BackWork BW,
                                                    long long b0) {
@@ -53,12 +72,16 @@ __global__ void __launch_bounds__(256) prep_kernel(const MatchLaunch L, const Ba
   const int rb = blockIdx.x % (N / RB);
   const long long b = b0 + s;
   const int tid = threadIdx.x;
-  if (L.level_idx != nullptr && __ldg(L.level_idx + b) != L.level) {
+  const int my = __ldg(L.mov_origin + 2 * b), mx = __ldg(L.mov_origin + 2 * b + 1);
+  const int ry = __ldg(L.ref_origin + 2 * b), rx = __ldg(L.ref_origin + 2 * b + 1);
+  // level and reference bounds through the shared guard (the moving window's
+  // bounds are its warped corners, below)
+  const int lv = L.level_idx != nullptr ? __ldg(L.level_idx + b) : L.level;
+  const int guard = window_check(N, lv, L.level, ry, rx, 0, 0, L.ref_h, L.ref_w, N, N);
+  if (guard == kWindowOtherLevel) {
     if (rb == 0 && tid == 0) BW.pre_status[s] = kStatusSkip;
     return;
   }
-  const int my = __ldg(L.mov_origin + 2 * b), mx = __ldg(L.mov_origin + 2 * b + 1);
-  const int ry = __ldg(L.ref_origin + 2 * b), rx = __ldg(L.ref_origin + 2 * b + 1);
   float th[6] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f};
   if (K.affine != nullptr) {
 #pragma unroll
@@ -67,15 +90,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const MatchLaunch L, const Ba
   const float c = 0.5f * N;
   const int cy = my + N / 2, cx = mx + N / 2;  // window centre: the integer base of every sample
   // bounds: the reference window, and the four corners of the warped moving window
-  bool ok = !(ry < 0 || rx < 0 || ry > L.ref_h - N || rx > L.ref_w - N);
-#pragma unroll
-  for (int corner = 0; corner < 4; ++corner) {
-    const float di = (corner & 1 ? N - 1 : 0) - c, dj = (corner & 2 ? N - 1 : 0) - c;
-    const float ly = th[0] * di + th[1] * dj + th[2];
-    const float lx = th[3] * di + th[4] * dj + th[5];
-    ok = ok && ly >= static_cast<float>(-cy) && lx >= static_cast<float>(-cx) &&
-         ly <= static_cast<float>(L.mov_h - 1 - cy) && lx <= static_cast<float>(L.mov_w - 1 - cx);
-  }
+  const bool ok = guard == SWIFT_WIN_OK && warped_inside<N>(th, cy, cx, L.mov_h, L.mov_w);
   if (rb == 0 && tid == 0) BW.pre_status[s] = ok ? SWIFT_WIN_OK : SWIFT_WIN_OUT_OF_BOUNDS;
   if (!ok) return;
   const TIn* mov = static_cast<const TIn*>(L.mov);
@@ -516,6 +531,16 @@ __global__ void __launch_bounds__(256) back_affine_kernel(const MatchLaunch L, c
   const int my = __ldg(L.mov_origin + 2 * b), mx = __ldg(L.mov_origin + 2 * b + 1);
   const float c = 0.5f * N;
   const int cy = my + N / 2, cx = mx + N / 2;  // window centre: the integer base of every sample
+  {
+    // the window guard again, from the launch's own arrays: the samples below
+    // are read only for a window of this level whose warped corners lie inside
+    const int lv = L.level_idx != nullptr ? __ldg(L.level_idx + b) : L.level;
+    if (lv != L.level || !warped_inside<N>(th, cy, cx, L.mov_h, L.mov_w)) {
+      if (tid < 6 && lv == L.level) K.grad_affine[6 * b + tid] = 0.f;
+      if (tid == 0) BW.gwin[s] = 0.0;
+      return;
+    }
+  }
   const TIn* mov = static_cast<const TIn*>(L.mov);
   const float* gmp = reinterpret_cast<const float*>(BW.fw.zr + s * N * N);
   __syncthreads();

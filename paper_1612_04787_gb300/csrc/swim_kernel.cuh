@@ -316,6 +316,16 @@ __device__ __forceinline__ float load_px(const TIn* p) {
   }
 }
 
+// window_check for window b of launch L, from its level and origin arrays
+// (patch mode: the level only)
+__device__ __forceinline__ int launch_window_check(const MatchLaunch& L, long long b, int n) {
+  const int lv = L.level_idx != nullptr ? __ldg(L.level_idx + b) : L.level;
+  if (L.patch_mode) return window_check(n, lv, L.level, 0, 0, 0, 0, n, n, n, n);
+  return window_check(n, lv, L.level, __ldg(L.ref_origin + 2 * b), __ldg(L.ref_origin + 2 * b + 1),
+                      __ldg(L.mov_origin + 2 * b), __ldg(L.mov_origin + 2 * b + 1), L.ref_h, L.ref_w, L.mov_h,
+                      L.mov_w);
+}
+
 template <int N, int C, bool BULK>
 constexpr size_t forward_smem_bytes() {
   using P = Plan2D<N, C>;
@@ -376,8 +386,8 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
       wi.mx = __ldg(L.mov_origin + 2 * w + 1);
       wi.ry = __ldg(L.ref_origin + 2 * w);
       wi.rx = __ldg(L.ref_origin + 2 * w + 1);
-      wi.ok = !(wi.my < 0 || wi.mx < 0 || wi.my > L.mov_h - N || wi.mx > L.mov_w - N || wi.ry < 0 ||
-                wi.rx < 0 || wi.ry > L.ref_h - N || wi.rx > L.ref_w - N);
+      wi.ok = window_check(N, L.level, L.level, wi.ry, wi.rx, wi.my, wi.mx, L.ref_h, L.ref_w, L.mov_h, L.mov_w) ==
+              SWIFT_WIN_OK;
     }
     sc->win[slot] = wi;
   };

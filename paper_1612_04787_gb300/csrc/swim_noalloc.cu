@@ -4,8 +4,10 @@
 // For callers that cannot allocate device memory: code that runs inside
 // another allocator's callback, real-time loops whose memory must not change
 // after start-up, or hosts where the memory pool is owned by a framework.
-// The entry point builds its small tables on the host, copies them into the
-// static array, and runs the same five streaming kernels as the plan path.
+// Every call computes its small taper and twiddle tables on the device (one
+// tiny kernel on the caller's stream, straight into the static array; no
+// host buffer is involved), then runs the same streaming kernels as the plan
+// path.
 #include <cuda_runtime.h>
 #include <initializer_list>
 #include <math.h>
@@ -45,16 +47,12 @@ long long capacity_for(int n) {
   return static_cast<long long>((kNoAllocBytes - kTableBytes - 4 * 256) / per);
 }
 
-void taper_values(int n, int apod, double alpha, double* a) {
-  for (int k = 0; k < n; ++k) a[k] = 1.0;
-  if (apod == SWIFT_APOD_NONE) return;
-  if (apod == SWIFT_APOD_HANN) alpha = 1.0;
-  const double ramp = alpha * n / 2.0;
-  for (int k = 0; k < n; ++k) {
-    if (k < ramp)
-      a[k] = 0.5 * (1.0 - cos(M_PI * k / ramp));
-    else if (k > n - ramp)
-      a[k] = 0.5 * (1.0 - cos(M_PI * (n - k) / ramp));
+// taper (n floats) and twiddle table (n complex, [m][j] with j < r1) of a level,
+// from the same definitions the plan path evaluates on the host
+__global__ void noalloc_tables_kernel(int n, int apod, double alpha, int r1, float* tap, float2* tw) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    tap[k] = static_cast<float>(swift::taper_value(n, apod, alpha, k));
+    tw[k] = swift::twiddle_entry(n, r1, k);
   }
 }
 
@@ -95,31 +93,17 @@ extern "C" swift_status swift_match_batch_noalloc(const swift_level* level, swif
   if (cudaGetDevice(&dev) != cudaSuccess) return SWIFT_ERR_CUDA;
   void* scratch = nullptr;
   if (scratch_address(dev, &scratch) != cudaSuccess) return SWIFT_ERR_CUDA;
-  if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-  // tables: taper then twiddles W_n^{j m} = exp(-2 pi i j m / n) stored [m][j]
+  // tables: taper at the start of the array, twiddles at byte 2048
   const int n = lv.n;
-  double a[512];
-  taper_values(n, lv.apod, lv.tukey_alpha, a);
-  double sum_a = 0.0;
-  unsigned char host_tables[kTableBytes];
-  float* tap = reinterpret_cast<float*>(host_tables);
-  float2* tw = reinterpret_cast<float2*>(host_tables + 2048);
-  for (int k = 0; k < n; ++k) {
-    sum_a += a[k];
-    tap[k] = static_cast<float>(a[k]);
-  }
   int r1 = 0, r2 = 0;
   swift::stream_radices(n, &r1, &r2);
-  for (int m = 0; m < r2; ++m)
-    for (int j = 0; j < r1; ++j) {
-      const double ang = -2.0 * M_PI * ((j * m) % n) / n;
-      tw[m * r1 + j] = make_float2(static_cast<float>(cos(ang)), static_cast<float>(sin(ang)));
-    }
+  double sum_a = 0.0;  // host copy of the taper's sum, for the mean's normalisation
+  for (int k = 0; k < n; ++k) sum_a += swift::taper_value(n, lv.apod, lv.tukey_alpha, k);
   unsigned char* base = static_cast<unsigned char*>(scratch);
-  if (cudaMemcpyAsync(base, host_tables, kTableBytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return SWIFT_ERR_CUDA;
+  noalloc_tables_kernel<<<1, 256, 0, st>>>(n, lv.apod, lv.tukey_alpha, r1, reinterpret_cast<float*>(base),
+                                           reinterpret_cast<float2*>(base + 2048));
 
   swift::MatchLaunch L;
   L.ref = ri.data;

@@ -33,10 +33,19 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  static unsigned m1 = 0, m2 = 0, m3 = 0;
+  // n <= 256: column pairs unpacked at load (whitening and the first inverse
+  // pass in registers); n = 512 keeps the per-column kernel (its pass B would
+  // hold 2 x 32 complex values per thread)
+  constexpr bool kPair = N <= 256;
+  static unsigned m1 = 0, m2 = 0, m3 = 0, m4 = 0;
   if ((e = smem_optin(stream_rows_kernel<N, TIn>, rows_smem<N, TIn>(), m1, dev)) != cudaSuccess) return e;
-  if ((e = smem_optin(stream_cols_kernel<N>, cols_smem<N>(), m2, dev)) != cudaSuccess) return e;
-  if ((e = smem_optin(stream_irows_kernel<N>, irows_smem<N>(), m3, dev)) != cudaSuccess) return e;
+  if constexpr (kPair) {
+    if ((e = smem_optin(stream_cpair_kernel<N>, cpair_smem<N>(), m2, dev)) != cudaSuccess) return e;
+  } else {
+    if ((e = smem_optin(stream_cols_kernel<N>, cols_smem<N>(), m2, dev)) != cudaSuccess) return e;
+  }
+  if ((e = smem_optin(stream_irows_kernel<N, false>, irows_smem<N>(), m3, dev)) != cudaSuccess) return e;
+  if ((e = smem_optin(stream_peak_kernel<N>, peak_smem<N>(), m4, dev)) != cudaSuccess) return e;
   auto mark = [&](int k) {
     if (W.ev) cudaEventRecord(W.ev[k], st);
   };
@@ -45,11 +54,15 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
   mark(1);
   stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
   mark(2);
-  stream_cols_kernel<N><<<S * G::NB2, G::T2, cols_smem<N>(), st>>>(L, W);
+  if constexpr (kPair) {
+    stream_cpair_kernel<N><<<S * PairGeom<N>::NB, PairGeom<N>::T, cpair_smem<N>(), st>>>(L, W);
+  } else {
+    stream_cols_kernel<N><<<S * G::NB2, G::T2, cols_smem<N>(), st>>>(L, W);
+  }
   mark(3);
-  stream_irows_kernel<N><<<S * G::NB3, 256, irows_smem<N>(), st>>>(L, W);
+  stream_irows_kernel<N, false><<<S * G::NB3, 256, irows_smem<N>(), st>>>(L, W);
   mark(4);
-  stream_final_kernel<N><<<S, 32, 0, st>>>(L, W);
+  stream_peak_kernel<N><<<S, PeakGeom<N>::T, peak_smem<N>(), st>>>(L, W);
   mark(5);
   return cudaGetLastError();
 }

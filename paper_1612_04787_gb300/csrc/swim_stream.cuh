@@ -30,7 +30,7 @@
 
 namespace swift {
 
-constexpr int kStatusSkip = -1;  // window of another level: no result written here
+constexpr int kStatusSkip = kWindowOtherLevel;  // window of another level: no result written here
 
 template <int N>
 struct StreamGeom {
@@ -84,8 +84,11 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
     put(L.pre_status[s], 0.f, 0.f);
     return;
   }
-  if (L.level_idx != nullptr && __ldg(L.level_idx + b) != L.level) {
-    put(kStatusSkip, 0.f, 0.f);
+  const int guard = launch_window_check(L, b, N);
+  if (guard != SWIFT_WIN_OK) {
+    // test hook: report a window of another level as OK without reading it, as
+    // a raced or stale workspace could; the row kernels' own guard must skip it
+    put(L.stale_ok && guard == kWindowOtherLevel ? SWIFT_WIN_OK : guard, 0.f, 0.f);
     return;
   }
   const TIn* mbase;
@@ -98,11 +101,6 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
   } else {
     const int my = __ldg(L.mov_origin + 2 * b), mx = __ldg(L.mov_origin + 2 * b + 1);
     const int ry = __ldg(L.ref_origin + 2 * b), rx = __ldg(L.ref_origin + 2 * b + 1);
-    if (my < 0 || mx < 0 || my > L.mov_h - N || mx > L.mov_w - N || ry < 0 || rx < 0 || ry > L.ref_h - N ||
-        rx > L.ref_w - N) {
-      put(SWIFT_WIN_OUT_OF_BOUNDS, 0.f, 0.f);
-      return;
-    }
     mbase = static_cast<const TIn*>(L.mov) + static_cast<long long>(my) * L.mov_pitch + mx;
     rbase = static_cast<const TIn*>(L.ref) + static_cast<long long>(ry) * L.ref_pitch + rx;
     mpitch = L.mov_pitch;
@@ -292,6 +290,15 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   const int tid = threadIdx.x;
   const float4 st = W.stats[s];
   if (stat_status(st) != SWIFT_WIN_OK) return;
+  {
+    // the window's level and bounds, from the launch's own arrays: a status
+    // word left by another call never makes this kernel read
+    const int guard = launch_window_check(L, b, N);
+    if (guard != SWIFT_WIN_OK) {
+      if (tid == 0) W.stats[s] = make_float4(0.f, 0.f, __int_as_float(guard), 0.f);
+      return;
+    }
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [RB][RS]
   float2* twid = slab + RB * RS;
@@ -624,9 +631,294 @@ __global__ void __launch_bounds__(StreamGeom<N>::T2) stream_cols_kernel(const Ma
 }
 
 // ---------------------------------------------------------------------------
+// K2 (plain forward, n = 64, 128, 256): column pairs with the Hermitian unpack
+// at load time
+// ---------------------------------------------------------------------------
+// A CTA owns CB values kx in [CB cb, CB cb + CB) of the half spectrum and reads
+// the row spectra of kx and of its partner n - kx.  Per row y the two real
+// windows' row spectra separate pointwise,
+//     a = Z[y][kx] + conj(Z[y][n - kx]) = 2 M_row[y][kx]
+//     b = Z[y][kx] - conj(Z[y][n - kx]) = 2i R_row[y][kx],
+// so one thread transforms the columns of a and b together, and after the
+// second radix pass holds M and R (times 2 and 2i) at the same bins
+// ky = k1 + R1 k2.  The cross power C = M conj(R) = i a conj(b) / 4, the
+// whitening and the first inverse pass then run in that thread's registers:
+// no partner exchange, and two barriers per CTA.  The 1/4 and 1/n^2 factors
+// ride in the whitening exponent: C |C|^-w / n^2 = C4 |C4|^-w 4^(w-1) / n^2
+// with C4 = i a conj(b).
+//
+// kx = 0 and kx = n/2 (both their own partners, both real columns after the
+// row transform) share the task lc = 0 of block 0: a = 2 (Re Z[y][0] + i Re
+// Z[y][n/2]), b = 2i (Im Z[y][0] + i Im Z[y][n/2]).  After the column
+// transform those tasks separate the two columns through the bins -ky (held by
+// the task k1' = -k1 mod R1), exchanged in shared memory, and whiten both; the
+// inverse input is G[.][0] + i G[.][n/2], whose inverse column transform is
+// H[y][0] + i H[y][n/2] (both real), the packed layout the inverse-row kernel
+// reads.
+template <int N>
+struct PairGeom {
+  using G = StreamGeom<N>;
+  static constexpr int R1 = G::R1, R2 = G::R2;
+  static constexpr int CB = N == 256 ? 16 : 32;  // kx per CTA
+  static constexpr int NB = (N / 2) / CB;        // CTAs per window
+  static constexpr int T = 256;
+  static constexpr int TA = CB * R2;  // pass A / A' tasks (line j or n2, column lc)
+  static constexpr int TB = CB * R1;  // pass B / B' tasks (k1, lc)
+  static constexpr int TW = R2 + 2;   // row stride of the transposed twiddle table (float2)
+  static_assert(TA % T == 0 && TB % T == 0, "whole task rounds");
+  static_assert(N / 2 % CB == 0, "column blocks");
+};
+
+__device__ __forceinline__ float whiten_scaled(float mag2, float half_w, float lscale) {
+  // |C4|^-w times 2^lscale (lg2 / ex2 hardware approximations; the input of
+  // lg2 is scaled by 2^64 below 2^-100, so neither instruction meets a
+  // subnormal)
+  if (!(mag2 > 0.f)) return 0.f;
+  const bool tiny = mag2 < 0x1p-100f;
+  float lg, f;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(tiny ? mag2 * 0x1p64f : mag2));
+  if (tiny) lg -= 64.f;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(fmaf(half_w, lg, lscale)));
+  return f;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch L, const StreamWork W) {
+  using P = PairGeom<N>;
+  constexpr int R1 = P::R1, R2 = P::R2, CB = P::CB, T = P::T, TW = P::TW;
+  constexpr int RB = P::TB / T;  // pass B rounds per thread
+  const long long s = blockIdx.x / P::NB;
+  const int cb = blockIdx.x % P::NB;
+  const int tid = threadIdx.x;
+  if (stat_status(W.stats[s]) != SWIFT_WIN_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* slab = reinterpret_cast<float4*>(smem_raw);  // [N][CB]: (a, b) after pass A
+  float2* slab2 = reinterpret_cast<float2*>(smem_raw);  // [N][CB]: G after pass B' (reuses slab)
+  float4* xbuf = slab + N * CB;                          // [R1][R2]: block 0, lc = 0
+  float2* twT = reinterpret_cast<float2*>(xbuf + N);     // [R1][TW]: W_n^(k1 n2)
+  for (int i = tid; i < N; i += T) twT[(i % R1) * TW + i / R1] = L.twiddle[i];
+  // pass A: task (j, lc) takes rows y = j + R2 m of columns kx and n - kx
+  const float2* zr = W.zr + s * N * N;
+#pragma unroll
+  for (int r = 0; r < P::TA / T; ++r) {
+    const int task = tid + r * T;
+    const int j = task / CB, lc = task % CB;
+    const int kx = CB * cb + lc;
+    const bool packed = kx == 0;  // columns 0 and n/2
+    const int kn = packed ? N / 2 : N - kx;
+    float2 a[R1], b[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+      const float2 zk = __ldcs(zr + (j + R2 * m) * N + kx);
+      const float2 zn = __ldcs(zr + (j + R2 * m) * N + kn);
+      if (packed) {
+        a[m] = make_float2(2.f * zk.x, 2.f * zn.x);
+        b[m] = make_float2(-2.f * zn.y, 2.f * zk.y);
+      } else {
+        a[m] = make_float2(zk.x + zn.x, zk.y - zn.y);
+        b[m] = make_float2(zk.x - zn.x, zk.y + zn.y);
+      }
+    }
+    dft<R1, -1>(a);
+    dft<R1, -1>(b);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) slab[(j + R2 * q) * CB + lc] = make_float4(a[q].x, a[q].y, b[q].x, b[q].y);
+  }
+  __syncthreads();
+  const float half_w = -0.5f * L.w;
+  // 2^lscale = 4^(w-1) / n^2
+  const float lscale = 2.f * L.w - 2.f - 2.f * static_cast<float>(__ffs(N) - 1);
+  // pass B (twiddles, DFT over n2), cross power, whitening and inverse pass B'
+  // (DFT over k2, conjugate twiddles), all on the task's R2 bins; the results
+  // stay in registers until every task has read the slab
+  float2 g[RB][R2];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    const int task = tid + r * T;
+    const int k1 = task / CB, lc = task % CB;
+    const float4* tw4 = reinterpret_cast<const float4*>(twT + k1 * TW);
+    float2 a[R2], b[R2];
+#pragma unroll
+    for (int q = 0; q < R2 / 2; ++q) {
+      const float4 t = tw4[q];
+      const float4 u = slab[(R2 * k1 + 2 * q) * CB + lc], v = slab[(R2 * k1 + 2 * q + 1) * CB + lc];
+      a[2 * q] = make_float2(u.x, u.y);
+      b[2 * q] = make_float2(u.z, u.w);
+      if (q > 0) {
+        a[2 * q] = cmul(a[2 * q], make_float2(t.x, t.y));
+        b[2 * q] = cmul(b[2 * q], make_float2(t.x, t.y));
+      }
+      a[2 * q + 1] = cmul(make_float2(v.x, v.y), make_float2(t.z, t.w));
+      b[2 * q + 1] = cmul(make_float2(v.z, v.w), make_float2(t.z, t.w));
+    }
+    dft<R2, -1>(a);
+    dft<R2, -1>(b);
+    if (cb == 0 && lc == 0) {
+      // columns 0 and n/2: separated after the barrier below
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) xbuf[k1 * R2 + k2] = make_float4(a[k2].x, a[k2].y, b[k2].x, b[k2].y);
+      continue;
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      // C4 = i a conj(b)
+      const float cr = fmaf(a[k2].x, b[k2].y, -a[k2].y * b[k2].x);
+      const float ci = fmaf(a[k2].x, b[k2].x, a[k2].y * b[k2].y);
+      const float f = whiten_scaled(fmaf(cr, cr, ci * ci), half_w, lscale);
+      a[k2] = make_float2(cr * f, ci * f);
+    }
+    dft<R2, +1>(a);
+#pragma unroll
+    for (int q = 0; q < R2 / 2; ++q) {
+      const float4 t = tw4[q];
+      g[r][2 * q] = q == 0 ? a[0] : cmulc(a[2 * q], make_float2(t.x, t.y));
+      g[r][2 * q + 1] = cmulc(a[2 * q + 1], make_float2(t.z, t.w));
+    }
+  }
+  __syncthreads();  // the slab is read; G goes into the same space
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    const int task = tid + r * T;
+    const int k1 = task / CB, lc = task % CB;
+    if (cb == 0 && lc == 0) continue;
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) slab2[(R2 * k1 + n2) * CB + lc] = g[r][n2];
+  }
+  if (cb == 0 && tid < R1) {
+    const int k1 = tid, k1p = (R1 - k1) % R1;
+    float2 gp[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      // bin -ky of ky = k1 + R1 k2
+      const int k2p = k1 == 0 ? (R2 - k2) % R2 : R2 - 1 - k2;
+      const float4 u = xbuf[k1 * R2 + k2], v = xbuf[k1p * R2 + k2p];
+      // a = 2 (M0 + i Mh), b = 2i (R0 + i Rh), with M0, Mh, R0, Rh the
+      // column spectra of kx = 0 and n/2 (Hermitian in ky)
+      const float2 m0 = make_float2(0.25f * (u.x + v.x), 0.25f * (u.y - v.y));
+      const float2 mh = make_float2(0.25f * (u.y + v.y), -0.25f * (u.x - v.x));
+      // q = b / 2i
+      const float2 q = make_float2(0.5f * u.w, -0.5f * u.z), qp = make_float2(0.5f * v.w, -0.5f * v.z);
+      const float2 r0 = make_float2(0.5f * (q.x + qp.x), 0.5f * (q.y - qp.y));
+      const float2 rh = make_float2(0.5f * (q.y + qp.y), -0.5f * (q.x - qp.x));
+      // C4 = 4 M conj(R) of each column
+      const float2 c0 = cmulc(m0, r0), ch = cmulc(mh, rh);
+      const float2 c40 = make_float2(4.f * c0.x, 4.f * c0.y), c4h = make_float2(4.f * ch.x, 4.f * ch.y);
+      const float f0 = (k1 == 0 && k2 == 0) ? 0.f : whiten_scaled(fmaf(c40.x, c40.x, c40.y * c40.y), half_w, lscale);
+      const float fh = whiten_scaled(fmaf(c4h.x, c4h.x, c4h.y * c4h.y), half_w, lscale);
+      // G[.][0] + i G[.][n/2]
+      gp[k2] = make_float2(c40.x * f0 - c4h.y * fh, c40.y * f0 + c4h.x * fh);
+    }
+    dft<R2, +1>(gp);
+    const float4* tw4 = reinterpret_cast<const float4*>(twT + k1 * TW);
+#pragma unroll
+    for (int q = 0; q < R2 / 2; ++q) {
+      const float4 t = tw4[q];
+      if (q > 0) gp[2 * q] = cmulc(gp[2 * q], make_float2(t.x, t.y));
+      gp[2 * q + 1] = cmulc(gp[2 * q + 1], make_float2(t.z, t.w));
+    }
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) slab2[(R2 * k1 + n2) * CB] = gp[n2];
+  }
+  __syncthreads();
+  // inverse pass A' -> H[y = n2 + R2 n1][kx]
+  float2* hw = W.h + s * N * (N / 2);
+#pragma unroll
+  for (int r = 0; r < P::TA / T; ++r) {
+    const int task = tid + r * T;
+    const int n2 = task / CB, lc = task % CB;
+    float2 v[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = slab2[(n2 + R2 * k1) * CB + lc];
+    dft<R1, +1>(v);
+    const int kx = CB * cb + lc;
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) hw[(n2 + R2 * n1) * (N / 2) + kx] = v[n1];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K3: inverse row transforms of row pairs (y, y + N/2), block argmax
 // ---------------------------------------------------------------------------
+// The row-pair steps are shared with K4, which recomputes the few rows around
+// the peak with the same instructions (so its values equal K3's bit for bit).
+//
+// irow_assemble: slab row p (< np) gets P = H[y1] + i H[y1 + n/2], the packed
+// pair of half rows completed by Hermitian symmetry, y1 = y1_of(p) < n/2.
+template <int N, int PB, int T, typename Y1>
+__device__ __forceinline__ void irow_assemble(const float2* __restrict__ hw, float2* slab, int np, Y1 y1_of,
+                                              int tid) {
+  using G = StreamGeom<N>;
+  constexpr int RS = G::RS;
+  constexpr int K = PB * (N / 2) / T;
+  static_assert(K * T == PB * (N / 2), "assembly split");
+  float2 h1[K], h2[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int e = tid + i * T;
+    const int p = e / (N / 2), kx = e % (N / 2);
+    if (p < np) {
+      const int y1 = y1_of(p), y2 = y1 + N / 2;
+      h1[i] = __ldcs(hw + y1 * (N / 2) + kx);
+      h2[i] = __ldcs(hw + y2 * (N / 2) + kx);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int e = tid + i * T;
+    const int p = e / (N / 2), kx = e % (N / 2);
+    if (p >= np) continue;
+    float2* row = slab + p * RS;
+    if (kx == 0) {
+      row[G::phys(0)] = make_float2(h1[i].x, h2[i].x);
+      row[G::phys(N / 2)] = make_float2(h1[i].y, h2[i].y);
+    } else {
+      row[G::phys(kx)] = make_float2(h1[i].x - h2[i].y, h1[i].y + h2[i].x);
+      row[G::phys(N - kx)] = make_float2(h1[i].x + h2[i].y, h2[i].x - h1[i].y);
+    }
+  }
+}
+
+// irow_passA: first inverse radix pass (DFT over m of x = j + R2 m), in place
+template <int N, int PB, int T>
+__device__ __forceinline__ void irow_passA(float2* slab, int np, int tid) {
+  using G = StreamGeom<N>;
+  constexpr int R1 = G::R1, R2 = G::R2, RS = G::RS;
+  constexpr int TA = PB * R2;
+#pragma unroll
+  for (int i = 0; i < (TA + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if (TA % T != 0 && task >= TA) break;
+    const int p = task / R2, j = task % R2;
+    if (p >= np) continue;
+    float2* row = slab + p * RS;
+    float2 v[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) v[m] = row[G::phys(j + R2 * m)];
+    dft<R1, +1>(v);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) row[G::phys(j + R2 * q)] = v[q];
+  }
+}
+
+// irow_passB: second inverse radix pass of one packed row for residue k1:
+// v[k2] = s[y1][x] + i s[y2][x] at x = k1 + R1 k2
 template <int N>
+__device__ __forceinline__ void irow_passB(const float2* row, const float2* twid, int k1,
+                                           float2 (&v)[StreamGeom<N>::R2]) {
+  using G = StreamGeom<N>;
+  constexpr int R1 = G::R1, R2 = G::R2;
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    const float2 x = row[G::phys(R2 * k1 + n2)];
+    v[n2] = n2 == 0 ? x : cmulc(x, twid[n2 * R1 + k1]);
+  }
+  dft<R2, +1>(v);
+}
+
+// WRITE_S: also store the match response s ([n][n] float32 in the Zr space),
+// which the backward pass and the tensor-core schedule read; the plain forward
+// keeps only the block argmax keys and sums.
+template <int N, bool WRITE_S = true>
 __global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, const StreamWork W) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, PB = G::PB, RS = G::RS, T = G::T;
@@ -640,54 +932,17 @@ __global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, 
   __shared__ unsigned long long wkey[T / 32];
   __shared__ double wsum[T / 32][2];
   for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
-  // assemble packed rows P = H[y1] + i H[y2] with Hermitian completion
   const float2* hw = W.h + s * N * (N / 2);
-  {
-    constexpr int K = PB * (N / 2) / T;
-    float2 h1[K], h2[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      const int e = tid + i * T;
-      const int p = e / (N / 2), kx = e % (N / 2);
-      const int y1 = pb * PB + p, y2 = y1 + N / 2;
-      h1[i] = __ldcs(hw + y1 * (N / 2) + kx);
-      h2[i] = __ldcs(hw + y2 * (N / 2) + kx);
-    }
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      const int e = tid + i * T;
-      const int p = e / (N / 2), kx = e % (N / 2);
-      float2* row = slab + p * RS;
-      if (kx == 0) {
-        row[G::phys(0)] = make_float2(h1[i].x, h2[i].x);
-        row[G::phys(N / 2)] = make_float2(h1[i].y, h2[i].y);
-      } else {
-        row[G::phys(kx)] = make_float2(h1[i].x - h2[i].y, h1[i].y + h2[i].x);
-        row[G::phys(N - kx)] = make_float2(h1[i].x + h2[i].y, h2[i].x - h1[i].y);
-      }
-    }
-  }
+  irow_assemble<N, PB, T>(hw, slab, PB, [&](int p) { return pb * PB + p; }, tid);
   __syncthreads();
-  constexpr int TA = PB * R2, TB = PB * R1;
-#pragma unroll
-  for (int i = 0; i < (TA + T - 1) / T; ++i) {
-    const int task = tid + i * T;
-    if (TA % T != 0 && task >= TA) break;
-    const int p = task / R2, j = task % R2;
-    float2* row = slab + p * RS;
-    float2 v[R1];
-#pragma unroll
-    for (int m = 0; m < R1; ++m) v[m] = row[G::phys(j + R2 * m)];
-    dft<R1, +1>(v);
-#pragma unroll
-    for (int q = 0; q < R1; ++q) row[G::phys(j + R2 * q)] = v[q];
-  }
+  irow_passA<N, PB, T>(slab, PB, tid);
   __syncthreads();
   float* surf = reinterpret_cast<float*>(W.zr + s * N * N);  // [N][N] response
   // running maxima of the y1 rows and of the y2 rows: each thread meets either
   // set in increasing row-major index, so a strict '>' keeps the smallest
   // index among equal values; one argmax key per set at the end
   // (initial index: the thread's first pixel of each set)
+  constexpr int TB = PB * R1;
   float bva = -INFINITY, bvb = -INFINITY;
   uint32_t bia = static_cast<uint32_t>((pb * PB + tid / R1) * N + tid % R1), bib = bia + (N / 2) * N;
   float s1 = 0.f, s2 = 0.f;  // sums of s and s^2 over every pixel of the block
@@ -696,20 +951,16 @@ __global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, 
     const int task = tid + i * T;
     if (TB % T != 0 && task >= TB) break;
     const int p = task / R1, k1 = task % R1;
-    const float2* row = slab + p * RS;
     float2 v[R2];
-#pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) {
-      const float2 x = row[G::phys(R2 * k1 + n2)];
-      v[n2] = n2 == 0 ? x : cmulc(x, twid[n2 * R1 + k1]);
-    }
-    dft<R2, +1>(v);
+    irow_passB<N>(slab + p * RS, twid, k1, v);
     const int y1 = pb * PB + p, y2 = y1 + N / 2;
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
       const int x = k1 + R1 * k2;
-      surf[y1 * N + x] = v[k2].x;
-      surf[y2 * N + x] = v[k2].y;
+      if constexpr (WRITE_S) {
+        surf[y1 * N + x] = v[k2].x;
+        surf[y2 * N + x] = v[k2].y;
+      }
       s1 += v[k2].x + v[k2].y;
       s2 = fmaf(v[k2].x, v[k2].x, fmaf(v[k2].y, v[k2].y, s2));
       if (v[k2].x > bva) {
@@ -746,6 +997,44 @@ __global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, 
       part[2] = static_cast<unsigned long long>(__double_as_longlong(t2));
     }
   }
+}
+
+// Result record from the peak (py, px, value pk), the background sums ta, tc
+// over tn pixels, and the wrapped neighbours nb = s(py-1, px), s(py+1, px),
+// s(py, px-1), s(py, px+1): SNR = (pk - mu) / sigma (population sigma; +inf
+// when sigma = 0 and the peak is above the mean), separable 3-point parabola
+// per axis clamped to [-1/2, 1/2] (0 when not concave), shifts in [-n/2, n/2).
+__device__ __forceinline__ swift_result window_result(int n, int py, int px, float pkf, double ta, double tc,
+                                                      double tn, const float* nb) {
+  const double mu = ta / tn;
+  const double var = tc / tn - mu * mu;
+  const double pk = static_cast<double>(pkf);
+  double snr;
+  if (var > 0.0) {
+    snr = (pk - mu) / sqrt(var);
+  } else {
+    snr = pk > mu ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
+  }
+  auto parab = [](double sm, double s0, double sp) -> double {
+    const double den = sm - 2.0 * s0 + sp;
+    if (!(den < 0.0)) return 0.0;
+    const double d = 0.5 * (sm - sp) / den;
+    return d < -0.5 ? -0.5 : (d > 0.5 ? 0.5 : d);
+  };
+  const double fy = parab(nb[0], pk, nb[1]);
+  const double fx = parab(nb[2], pk, nb[3]);
+  const int dy = py < n / 2 ? py : py - n;
+  const int dx = px < n / 2 ? px : px - n;
+  swift_result r;
+  r.dy = dy;
+  r.dx = dx;
+  r.sy = static_cast<float>(dy + fy);
+  r.sx = static_cast<float>(dx + fx);
+  r.snr = static_cast<float>(snr);
+  r.peak = static_cast<float>(pk);
+  r.status = SWIFT_WIN_OK;
+  r.reserved = 0;
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -798,38 +1087,154 @@ __global__ void __launch_bounds__(256) stream_final_kernel(const MatchLaunch L, 
   dc = warp_sum_f64(dc);
   dn = warp_sum_f64(dn);
   if (lane == 0) {
-    const double tn = static_cast<double>(N) * N - dn;
-    ta -= da;
-    tc -= dc;
-    const double mu = ta / tn;
-    const double var = tc / tn - mu * mu;
-    const double pk = static_cast<double>(key_value(gk));
-    double snr;
-    if (var > 0.0) {
-      snr = (pk - mu) / sqrt(var);
-    } else {
-      snr = pk > mu ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
+    const float nb[4] = {surf[((py + N - 1) & (N - 1)) * N + px], surf[((py + 1) & (N - 1)) * N + px],
+                         surf[py * N + ((px + N - 1) & (N - 1))], surf[py * N + ((px + 1) & (N - 1))]};
+    *out = window_result(N, py, px, key_value(gk), ta - da, tc - dc, static_cast<double>(N) * N - dn, nb);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4 (plain forward): peak, SNR and subpixel fit without a stored response
+// ---------------------------------------------------------------------------
+// K3 keeps only block argmax keys and the sums of s and s^2.  The exclusion
+// disc (radius r) and the parabola need s on the rows within R = floor(r) + 1
+// of the peak; this kernel recomputes those rows from H with K3's own row-pair
+// steps (the values equal K3's bit for bit, so total minus disc is exact up to
+// the FP64 sums) -- a pruned inverse: about 2R + 1 of the n/2 row pairs
+// instead of a full n x n response written and read back.
+template <int N>
+struct PeakGeom {
+  static constexpr int T = 128;  // threads per window
+  static constexpr int PB = 8;   // row pairs per chunk
+};
+
+template <int N>
+__global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L, const StreamWork W) {
+  using G = StreamGeom<N>;
+  constexpr int R1 = G::R1, R2 = G::R2, RS = G::RS;
+  constexpr int PB = PeakGeom<N>::PB, T = PeakGeom<N>::T;
+  constexpr int TB = PB * R1;
+  const long long s = blockIdx.x;
+  const long long b = W.b0 + s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int st = stat_status(W.stats[s]);
+  if (st == kStatusSkip) return;
+  swift_result* out = L.out + b;
+  if (st != SWIFT_WIN_OK) {
+    if (tid == 0) {
+      swift_result r = {0, 0, 0.f, 0.f, 0.f, 0.f, st, 0};
+      *out = r;
     }
-    auto parab = [](double sm, double s0, double sp) -> double {
-      const double den = sm - 2.0 * s0 + sp;
-      if (!(den < 0.0)) return 0.0;
-      const double d = 0.5 * (sm - sp) / den;
-      return d < -0.5 ? -0.5 : (d > 0.5 ? 0.5 : d);
-    };
-    const double fy = parab(surf[((py + N - 1) & (N - 1)) * N + px], pk, surf[((py + 1) & (N - 1)) * N + px]);
-    const double fx = parab(surf[py * N + ((px + N - 1) & (N - 1))], pk, surf[py * N + ((px + 1) & (N - 1))]);
-    const int dy = py < N / 2 ? py : py - N;
-    const int dx = px < N / 2 ? px : px - N;
-    swift_result r;
-    r.dy = dy;
-    r.dx = dx;
-    r.sy = static_cast<float>(dy + fy);
-    r.sx = static_cast<float>(dx + fx);
-    r.snr = static_cast<float>(snr);
-    r.peak = static_cast<float>(pk);
-    r.status = SWIFT_WIN_OK;
-    r.reserved = 0;
-    *out = r;
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* slab = reinterpret_cast<float2*>(smem_raw);  // [PB][RS]
+  float2* twid = slab + PB * RS;
+  __shared__ unsigned long long s_key;
+  __shared__ double s_tot[2];
+  __shared__ double s_red[T / 32][3];
+  __shared__ float s_nb[4];  // s at (py - 1, px), (py + 1, px), (py, px - 1), (py, px + 1)
+  for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
+  if (warp == 0) {
+    // global argmax and totals from the block partials of K3
+    unsigned long long gk = 0ull;
+    double ta = 0.0, tc = 0.0;
+    for (int k = lane; k < G::NB3; k += 32) {
+      const unsigned long long* part = W.part + 3 * (s * G::NB3 + k);
+      const unsigned long long v = part[0];
+      gk = v > gk ? v : gk;
+      ta += __longlong_as_double(static_cast<long long>(part[1]));
+      tc += __longlong_as_double(static_cast<long long>(part[2]));
+    }
+    gk = warp_max_u64(gk);
+    ta = warp_sum_f64(ta);
+    tc = warp_sum_f64(tc);
+    if (lane == 0) {
+      s_key = gk;
+      s_tot[0] = ta;
+      s_tot[1] = tc;
+    }
+  }
+  __syncthreads();
+  const unsigned long long gk = s_key;
+  const uint32_t pidx = key_index(gk);
+  const int py = static_cast<int>(pidx / N), px = static_cast<int>(pidx % N);
+  // rows within R of the peak: the disc (dy^2 + dx^2 <= r2, so |dy| <=
+  // floor(sqrt(r2))) and the parabola's neighbours (|dy| <= 1)
+  int R = static_cast<int>(sqrtf(L.radius2));
+  while ((R + 1) * (R + 1) <= static_cast<int>(L.radius2)) ++R;
+  while (R * R > static_cast<int>(L.radius2)) --R;
+  R = R < 1 ? 1 : R;
+  // row pairs (y, y + n/2) holding the rows py - R .. py + R: consecutive pair indices
+  const int npairs = 2 * R + 1 < N / 2 ? 2 * R + 1 : N / 2;
+  const int p0 = (py - R) & (N / 2 - 1);
+  const float2* hw = W.h + s * N * (N / 2);
+  double da = 0.0, dc = 0.0, dn = 0.0;
+  for (int c0 = 0; c0 < npairs; c0 += PB) {
+    const int np = npairs - c0 < PB ? npairs - c0 : PB;
+    irow_assemble<N, PB, T>(hw, slab, np, [&](int p) { return (p0 + c0 + p) & (N / 2 - 1); }, tid);
+    __syncthreads();
+    irow_passA<N, PB, T>(slab, np, tid);
+    __syncthreads();
+    // pass B into registers, then the outputs back into the slab in natural
+    // order (slab row p, position phys(x): s[y1][x] + i s[y1 + n/2][x])
+    constexpr int KB = (TB + T - 1) / T;
+    float2 v[KB][R2];
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+      const int task = tid + i * T;
+      if ((TB % T != 0 && task >= TB) || task / R1 >= np) continue;
+      irow_passB<N>(slab + (task / R1) * RS, twid, task % R1, v[i]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+      const int task = tid + i * T;
+      if ((TB % T != 0 && task >= TB) || task / R1 >= np) continue;
+      float2* row = slab + (task / R1) * RS;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) row[G::phys(task % R1 + R1 * k2)] = v[i][k2];
+    }
+    __syncthreads();
+    // disc pixels of this chunk's rows (FP64 sums) and the peak's neighbours
+    if (warp == 0) {
+      const int D = 2 * R + 1;
+      for (int e = lane; e < D * D; e += 32) {
+        const int dy = e / D - R, dx = e % D - R;
+        const int y = (py + dy) & (N - 1), x = (px + dx) & (N - 1);
+        const int slot = ((y & (N / 2 - 1)) - p0 - c0) & (N / 2 - 1);
+        if (slot >= np) continue;  // a row of another chunk
+        const float2 pv = slab[slot * RS + G::phys(x)];
+        const float val = y >= N / 2 ? pv.y : pv.x;
+        if (dy * dy + dx * dx <= static_cast<int>(L.radius2)) {
+          const double d = val;
+          da += d;
+          dc += d * d;
+          dn += 1.0;
+        }
+        if (dx == 0 && (dy == -1 || dy == 1)) s_nb[dy < 0 ? 0 : 1] = val;
+        if (dy == 0 && (dx == -1 || dx == 1)) s_nb[dx < 0 ? 2 : 3] = val;
+      }
+    }
+    __syncthreads();  // the slab is reused by the next chunk
+  }
+  da = warp_sum_f64(da);
+  dc = warp_sum_f64(dc);
+  dn = warp_sum_f64(dn);
+  if (lane == 0) {
+    s_red[warp][0] = da;
+    s_red[warp][1] = dc;
+    s_red[warp][2] = dn;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 1; k < T / 32; ++k) {
+      da += s_red[k][0];
+      dc += s_red[k][1];
+      dn += s_red[k][2];
+    }
+    *out = window_result(N, py, px, key_value(gk), s_tot[0] - da, s_tot[1] - dc, static_cast<double>(N) * N - dn,
+                         s_nb);
   }
 }
 
@@ -846,6 +1251,15 @@ template <int N>
 constexpr size_t cols_smem() {
   using G = StreamGeom<N>;
   return sizeof(float2) * (N * (2 * G::CB + 8) + G::R1 * (G::R2 + 2));
+}
+template <int N>
+constexpr size_t cpair_smem() {
+  using P = PairGeom<N>;
+  return sizeof(float4) * N * P::CB + sizeof(float4) * N + sizeof(float2) * P::R1 * P::TW;
+}
+template <int N>
+constexpr size_t peak_smem() {
+  return sizeof(float2) * (PeakGeom<N>::PB * StreamGeom<N>::RS + N);
 }
 template <int N>
 constexpr size_t irows_smem() {

@@ -299,6 +299,13 @@ __global__ void __launch_bounds__(256, tcf_minb<N, true>()) tcf_rows_kernel(cons
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float4 st = W.stats[s];
   if (stat_status(st) != SWIFT_WIN_OK) return;
+  {
+    const int guard = launch_window_check(L, b, N);  // level and bounds from the launch's arrays
+    if (guard != SWIFT_WIN_OK) {
+      if (tid == 0) W.stats[s] = make_float4(0.f, 0.f, __int_as_float(guard), 0.f);
+      return;
+    }
+  }
   extern __shared__ __align__(16) unsigned char tcf_smem[];
   float2* tile = reinterpret_cast<float2*>(tcf_smem);  // [N][RT], swizzled columns
   float* tap = reinterpret_cast<float*>(tile + N * RT);

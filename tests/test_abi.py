@@ -91,3 +91,39 @@ def test_mir_argument_errors_before_any_launch():
     assert lib.swift_fit_affine_update(dummy, dummy, dummy, dummy, -1, dummy, dummy, None) == _lib.SWIFT_ERR_INVALID_ARG
     assert lib.swift_fit_affine_update(None, None, None, None, 0, None, None, None) == _lib.SWIFT_OK
     assert lib.swift_correspondences(None, None, None, 4, 64, 0.0, None, None, None, None) == _lib.SWIFT_ERR_INVALID_ARG
+
+
+def test_window_guard_rule():
+    """The guard every origin-reading kernel applies (swift_window_check):
+    hand-picked edges of the bounds, negative and huge origins, images
+    smaller than the window, and level mismatches (which win over bounds)."""
+    import paper_1612_04787_gb300 as swift
+    wc = swift.window_check
+    n, H, W = 256, 1024, 768
+    ok, oob, other = 0, 1, -1
+    cases = [
+        ((0, 0), (0, 0), ok),
+        ((H - n, W - n), (H - n, W - n), ok),          # last fitting origin
+        ((H - n + 1, 0), (0, 0), oob),                 # one row too far (reference)
+        ((0, W - n + 1), (0, 0), oob),
+        ((0, 0), (H - n + 1, 0), oob),                 # moving window
+        ((0, 0), (0, W - n + 1), oob),
+        ((-1, 0), (0, 0), oob),                        # negative origins
+        ((0, -1), (0, 0), oob),
+        ((0, 0), (-1, 5), oob),
+        ((0, 0), (5, -2147483648), oob),
+        ((2147483647, 0), (0, 0), oob),                # no overflow into "inside"
+        ((0, 2147483647), (0, 0), oob),
+    ]
+    for ro, mo, want in cases:
+        assert wc(n, 2, 2, ro, mo, (H, W), (H, W)) == want, (ro, mo)
+    # moving image smaller than the reference image
+    assert wc(n, 0, 0, (H - n, 0), (H - n, 0), (H, W), (H - 1, W)) == oob
+    # an image smaller than the window holds no window
+    assert wc(n, 0, 0, (0, 0), (0, 0), (n - 1, W), (H, W)) == oob
+    assert wc(n, 0, 0, (0, 0), (0, 0), (H, W), (H, n - 1)) == oob
+    # another level: skipped whatever its origins
+    for ro, mo, _ in cases:
+        assert wc(n, 1, 2, ro, mo, (H, W), (H, W)) == other
+        assert wc(n, 3, 2, ro, mo, (H, W), (H, W)) == other
+    assert wc(n, -5, 0, (0, 0), (0, 0), (H, W), (H, W)) == other

@@ -106,3 +106,23 @@ def test_noalloc_512_matches_plan_path():
     big = torch.zeros((8, 512, 512), dtype=torch.float32, device=DEV)
     out8 = torch.empty((8, 8), dtype=torch.int32, device=DEV)
     assert noalloc_match(lv, "f32", big, big, None, None, out8) == _lib.SWIFT_ERR_CAPACITY
+
+
+def test_noalloc_64_without_taper_matches_plan_path():
+    """64 x 64 windows with apodisation NONE: the tables the entry point
+    computes on the device for this level equal the plan's host-built ones in
+    effect (same results within the parity tolerances), on two calls in a row."""
+    a, b = synth.em_section_pair(512, seed_content=71, seed_warp=72, seed_noise=(73, 74))
+    ro = synth.random_origins(40, 512, 512, 64, seed=75)
+    mo = np.clip(ro + np.random.default_rng(76).integers(-6, 7, ro.shape), 0, 448).astype(np.int32)
+    ta, tb = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    tro, tmo = torch.from_numpy(ro).to(DEV), torch.from_numpy(mo).to(DEV)
+    lv = swift.Level(64, 0.65, "none", 1.0, 3.0)
+    plan = swift.Plan([lv], dtype="u8", max_windows=len(ro))
+    plan.set_schedule(0, "stream")
+    want = swift.decode(plan.match(ta, tb, tro, tmo))
+    for _ in range(2):
+        out = torch.full((len(ro), 8), -7, dtype=torch.int32, device=DEV)
+        assert noalloc_match(lv, "u8", ta, tb, tro, tmo, out) == _lib.SWIFT_OK
+        torch.cuda.synchronize()
+        assert_close(swift.decode(out), want)
