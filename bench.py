@@ -288,11 +288,14 @@ class Sections:
     name = "sections"
     dominant_n = 256
 
-    def __init__(self, torch, swift, dev, pairs=1, windows=0, precision="fp32"):
+    def __init__(self, torch, swift, dev, pairs=1, windows=0, precision="fp32", rank=0):
         import synth
         self.n, self.w, self.r, self.size, self.stride = 256, 0.65, 3.0, 4096, 128
+        # the job is world x pairs section pairs: rank r matches pairs r*pairs .. r*pairs + pairs - 1
+        # (its own shard; no collective on the data path)
+        first = rank * pairs
         self.secs = [synth.em_section_pair(self.size, seed_content=10 * p, seed_warp=1 + 10 * p,
-                                           seed_noise=(2 + 10 * p, 3 + 10 * p)) for p in range(pairs)]
+                                           seed_noise=(2 + 10 * p, 3 + 10 * p)) for p in range(first, first + pairs)]
         org = synth.grid_origins(self.size, self.n, self.stride)
         self.org = org[:windows] if windows > 0 else org
         g = (self.size - self.n) // self.stride + 1
@@ -627,9 +630,76 @@ class Warp:
         return movs, refs, self.n, self.w, self.r
 
 
+class Whitening:
+    """The whitening-exponent study (Sec. III, Fig. 2) as a batched workload:
+    damaged 256 x 256 pairs matched at 11 exponents in one call."""
+    name = "whitening"
+    dominant_n = 256
+
+    def __init__(self, torch, swift, dev, count=256, **_):
+        import synth
+        self.n, self.w, self.r = 256, 0.6, 3.0
+        self.exps = [round(0.1 * k, 1) for k in range(11)]
+        ref, mov, self.shifts = synth.damaged_pairs(self.n, count, seed=90)
+        self.ref_np, self.mov_np = ref, mov
+        E = len(self.exps)
+        self.windows = count * E
+        self.description = (f"{count} damaged 256x256 uint8 pairs (illumination gradient, dark fold, smeared half "
+                            f"plane, shot noise; known integer shifts) matched at {E} whitening exponents "
+                            f"0, 0.1, ..., 1 in one call ({self.windows} windows)")
+        self.plan = swift.Plan([swift.Level(self.n, w, "hann", 1.0, self.r) for w in self.exps], dtype="u8",
+                               max_windows=self.windows)
+        T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)  # noqa: E731
+        self.dref = T(np.tile(ref, (E, 1, 1)))
+        self.dmov = T(np.tile(mov, (E, 1, 1)))
+        self.lvl = T(np.repeat(np.arange(E, dtype=np.int32), count))
+        self.out = torch.empty((self.windows, 8), dtype=torch.int32, device=dev)
+        self.hout = torch.empty((self.windows, 8), dtype=torch.int32).pin_memory()
+        self.flops = flops_per_pair(self.n) * self.windows
+        self.launches_per_step = 5 * E * -(-self.windows // 2048)
+        self.count = count
+        self.config = {"window": 256, "windows_per_step": self.windows, "pairs": count, "exponents": self.exps,
+                       "input": "uint8"}
+
+    def step(self, stream):
+        E = len(self.exps)
+        self.plan.match([self.dref] * E, [self.dmov] * E, level=self.lvl, out=self.out, stream=stream)
+
+    def e2e_step(self, torch, stream):
+        if not hasattr(self, "href"):
+            self.href, self.hmov = self.dref.cpu().pin_memory(), self.dmov.cpu().pin_memory()
+        self.dref.copy_(self.href, non_blocking=True)
+        self.dmov.copy_(self.hmov, non_blocking=True)
+        self.step(stream)
+        self.hout.copy_(self.out, non_blocking=True)
+        stream.synchronize()
+
+    def io_bytes(self):
+        return 2 * self.dref.numel(), self.windows * 32
+
+    def ok_fraction(self, swift):
+        g = swift.decode(self.out)
+        E, P = len(self.exps), self.count
+        curve = []
+        for e, w in enumerate(self.exps):
+            sl = slice(e * P, (e + 1) * P)
+            hit = (np.abs(g["sy"][sl] - self.shifts[:, 0]) <= 1.5) & (np.abs(g["sx"][sl] - self.shifts[:, 1]) <= 1.5)
+            curve.append({"w": w, "median_snr": round(float(np.median(g["snr"][sl])), 3),
+                          "located_within_1.5px": round(float(hit.mean()), 4)})
+        self.config["snr_curve"] = curve
+        return float((g["status"] == 0).mean())
+
+    def oracle_windows(self, k):
+        k = min(k, self.count)
+        lvl = self.exps.index(self.w)
+        return ([m.astype(np.float64) for m in self.mov_np[:k]], [r.astype(np.float64) for r in self.ref_np[:k]],
+                self.n, self.exps[lvl], self.r)
+
+
 def make_workload(name, torch, swift, dev, args):
     if name == "sections":
-        return Sections(torch, swift, dev, pairs=args.pairs, windows=args.windows, precision=args.precision)
+        return Sections(torch, swift, dev, pairs=args.pairs, windows=args.windows, precision=args.precision,
+                        rank=int(os.environ.get("RANK", "0")))
     if name == "noise64":
         return Noise64(torch, swift, dev)
     if name == "pyramid":
@@ -638,6 +708,8 @@ def make_workload(name, torch, swift, dev, args):
         return Patches(torch, swift, dev, n=int(name[7:]), count=args.windows or 8192, precision=args.precision)
     if name == "warp":
         return Warp(torch, swift, dev, count=args.windows or 2048)
+    if name == "whitening":
+        return Whitening(torch, swift, dev, count=args.windows or 256)
     raise ValueError(name)
 
 
@@ -977,9 +1049,10 @@ def dist_setup():
 
 
 def aggregate_over_ranks(total_ms, windows, steps, world, device=None):
-    """Weak scaling: every rank runs the whole workload on its own GPU; the job
-    time is the slowest rank's (all-reduce MAX), and the value counts the
-    windows of all ranks.  Returns (job ms, windows/s)."""
+    """Weak scaling: every rank matches its own shard of the job (its own
+    section pairs, the same count per rank) on its own GPU; the job time is
+    the slowest rank's (all-reduce MAX), and the value counts the windows of
+    all ranks.  Returns (job ms, windows/s)."""
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -1036,7 +1109,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sections",
-                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "mir", "remod",
+                    choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "whitening", "mir", "remod",
                              "align"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2", "fp16x2"])
     ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (sections workload)")

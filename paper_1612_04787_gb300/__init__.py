@@ -113,6 +113,11 @@ class Plan:
         movs = mov if isinstance(mov, (list, tuple)) else [mov]
         if len(refs) != len(movs):
             raise ValueError("ref and mov need one image per level")
+        nlv = len(self.levels)
+        if len(refs) == 1 and nlv > 1:
+            refs, movs = list(refs) * nlv, list(movs) * nlv  # one image serves every level
+        if len(refs) != nlv:
+            raise ValueError(f"the plan has {nlv} levels: give one image per level (or one for all)")
         if patch:
             B = refs[0].shape[0]
         else:
@@ -281,6 +286,27 @@ def window_check(n: int, level: int, want_level: int, ref_origin, mov_origin, re
     mo = (C.c_int32 * 2)(*[int(v) for v in mov_origin])
     return int(lib.swift_window_check(int(n), int(level), int(want_level), ro, mo, int(ref_shape[0]),
                                       int(ref_shape[1]), int(mov_shape[0]), int(mov_shape[1])))
+
+
+def whitening_sweep(ref, mov, n: int, exponents, apod: str = "hann", tukey_alpha: float = 1.0,
+                    snr_exclusion_radius: float = 3.0, stream=None):
+    """Match every patch pair at every whitening exponent in one call.
+
+    ``ref`` / ``mov``: [P, n, n] uint8 or float32 CUDA stacks.  One plan level
+    per exponent (same window size), a batch of P * E windows whose level index
+    selects the exponent (the pairs repeated E times on the device).  Returns
+    a [E, P, 8] int32 result tensor (row e holds exponent ``exponents[e]``).
+    """
+    ws = [float(w) for w in exponents]
+    P, E = int(ref.shape[0]), len(ws)
+    dtype = "u8" if ref.dtype == torch.uint8 else "f32"
+    plan = Plan([Level(n, w, apod, tukey_alpha, snr_exclusion_radius) for w in ws], dtype=dtype,
+                max_windows=max(1, P * E))
+    rr = ref.unsqueeze(0).expand(E, P, n, n).reshape(E * P, n, n).contiguous()
+    mm = mov.unsqueeze(0).expand(E, P, n, n).reshape(E * P, n, n).contiguous()
+    lvl = torch.arange(E, dtype=torch.int32, device=ref.device).repeat_interleave(P)
+    out = plan.match([rr] * E, [mm] * E, level=lvl, stream=stream)
+    return out.view(E, P, 8)
 
 
 def decode(res) -> dict:

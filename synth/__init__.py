@@ -29,6 +29,7 @@ __all__ = [
     "shifted_patches",
     "section_stack",
     "affine_params",
+    "damaged_pairs",
 ]
 
 
@@ -288,3 +289,47 @@ def affine_params(count: int, seed: int, max_offset: float = 2.0,
     t = np.where(frac > 0.95, t - 0.05, t)
     c, s = np.cos(th), np.sin(th)
     return np.stack([c, -s, t[:, 0], s, c, t[:, 1]], axis=1).astype(np.float32)
+
+
+# --------------------------------------------------------------------------- #
+# damaged pairs (whitening-exponent study, the Fig. 2 setting)
+# --------------------------------------------------------------------------- #
+def damaged_pairs(n: int, count: int, seed: int, size: int | None = None, max_shift: int = 24):
+    """Reference patches and damaged, shifted copies of them (uint8).
+
+    The paper's Fig. 2 locates a damaged region B inside an undamaged area A at
+    several whitening exponents.  Stand-in: from one clean EM-like section
+    (``em_clean``, content seed ``seed + 1``) the reference is the n x n tile
+    at a random origin; the moving patch is the tile shifted by an integer
+    d ~ U{-max_shift..max_shift}^2 (moving(y) = clean(y0 - d + y), so the
+    match finds +d) and damaged by
+      * a smooth illumination gradient (x 1 +- 0.25 across the patch),
+      * a dark fold: a band 4-10 px wide at a random angle, x 0.25,
+      * a smeared half plane (Gaussian blur, sigma 2.5 px),
+    then shot noise at SNR 3 (reference: SNR 6).  Returns
+    (ref [count,n,n] uint8, mov [count,n,n] uint8, d [count,2] int64 as (dy, dx)).
+    """
+    rng = np.random.default_rng(seed)
+    size = size or max(1024, 4 * n)
+    clean = em_clean(size, seed=seed + 1)
+    ref = np.empty((count, n, n), np.uint8)
+    mov = np.empty((count, n, n), np.uint8)
+    shifts = np.empty((count, 2), np.int64)
+    yy, xx = np.mgrid[0:n, 0:n] / n
+    margin = max_shift + 16
+    for i in range(count):
+        y0, x0 = rng.integers(margin, size - n - margin, 2)
+        d = rng.integers(-max_shift, max_shift + 1, 2)
+        a = clean[y0:y0 + n, x0:x0 + n]
+        b = clean[y0 - d[0]:y0 - d[0] + n, x0 - d[1]:x0 - d[1] + n].copy()
+        phi = rng.uniform(0.0, 2.0 * np.pi, 2)
+        b = b * (1.0 + 0.5 * ((yy - 0.5) * np.cos(phi[0]) + (xx - 0.5) * np.sin(phi[1])))
+        th, c, half_width = rng.uniform(0.0, np.pi), rng.uniform(0.3, 0.7), rng.uniform(4.0, 10.0)
+        band = np.abs((yy - c) * np.cos(th) + (xx - 0.5) * np.sin(th)) < half_width / n
+        b[band] *= 0.25
+        side = ((yy - 0.5) * np.sin(th) - (xx - 0.5) * np.cos(th)) > rng.uniform(-0.2, 0.2)
+        b = np.where(side, ndimage.gaussian_filter(b, 2.5), b)
+        ref[i] = shot_noise(np.clip(a, 0, 255), seed=seed * 1000 + 2 * i, snr=6.0)
+        mov[i] = shot_noise(np.clip(b, 0, 255), seed=seed * 1000 + 2 * i + 1, snr=3.0)
+        shifts[i] = d
+    return ref, mov, shifts
