@@ -170,7 +170,7 @@ typedef struct {
 
 typedef struct swift_plan_s* swift_plan;
 
-/* Create a plan for up to n_levels (1..8) matching levels.  Builds the taper
+/* Create a plan for up to n_levels (1..16) matching levels.  Builds the taper
  * and twiddle tables (FP64 on the host, stored as FP32 on the current device).
  * max_windows bounds n_windows of later calls (> 0).  Returns
  * SWIFT_ERR_UNSUPPORTED for a window size or precision this build lacks

@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr int kMaxLevels = 8;
+constexpr int kMaxLevels = 16;
 constexpr int kTimingSets = 1024;
 constexpr int kNumSizes = 4;
 constexpr int kSizes[kNumSizes] = {64, 128, 256, 512};
