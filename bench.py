@@ -71,7 +71,8 @@ def kernel_flops(n: int) -> dict:
     m = n * n
     half = 5.0 * m * math.log2(n)  # n complex FFTs of length n
     return {"stats": 2.5 * m, "rows": half + 5.0 * m, "cols": 1.5 * half + 15.0 * m,
-            "irows": 0.5 * half + 5.0 * m, "final": 2.5 * m, "fused": flops_per_pair(n)}
+            "irows": 0.5 * half + 5.0 * m, "final": 2.5 * m, "fused": flops_per_pair(n),
+            "persistent": flops_per_pair(n)}
 
 
 def fp32_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
@@ -430,7 +431,7 @@ class Pyramid:
     name = "pyramid"
     dominant_n = 256
 
-    def __init__(self, torch, swift, dev, **_):
+    def __init__(self, torch, swift, dev, schedule="default", **_):
         import synth
         a, b = synth.em_section_pair(4096)
         self.imgs = [(synth.box_downsample(a, 4), synth.box_downsample(b, 4)),
@@ -441,26 +442,36 @@ class Pyramid:
             o = synth.grid_origins(ia.shape[0], lv.n, lv.n // 4)
             orgs.append(o)
             lvls.append(np.full(len(o), k, np.int32))
-        self.org = np.concatenate(orgs).astype(np.int32)
+        self.org = np.concatenate(orgs).astype(np.int32)  # sorted by level
         self.lvl = np.concatenate(lvls)
+        self.offs = [0] + list(np.cumsum([len(o) for o in orgs]))
         self.windows = len(self.org)
         self.description = (f"pyramid of one section pair at 1024^2 / 2048^2 / 4096^2 with 64 / 128 / 256 windows "
-                            f"at stride n/4 ({self.windows} windows), w = 0.5 / 0.65 / 0.8, one CUDA-graph "
-                            f"replay per step")
+                            f"at stride n/4 ({self.windows} windows, sorted by level), w = 0.5 / 0.65 / 0.8, "
+                            f"one CUDA-graph replay per step")
         self.plan = swift.Plan(self.levels, dtype="u8", max_windows=self.windows)
         T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)  # noqa: E731
         self.da = [T(x[0]) for x in self.imgs]
         self.db = [T(x[1]) for x in self.imgs]
         self.dorg, self.dlvl = T(self.org), T(self.lvl)
-        self.chosen, _ = self.plan.autotune(self.da, self.db, self.dorg, self.dorg, level=self.dlvl)
+        if schedule == "default":
+            self.chosen, _ = self.plan.autotune(self.da, self.db, self.dorg, self.dorg, level=self.dlvl,
+                                                level_offsets=self.offs)
+        else:  # one schedule for every level, no autotuning
+            for l in range(len(self.levels)):
+                self.plan.set_schedule(l, schedule)
+            self.chosen = [schedule] * len(self.levels)
         self.cap_stream = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(self.cap_stream):
             self.out = self.plan.capture(self.da, self.db, self.dorg, self.dorg, level=self.dlvl,
-                                         stream=self.cap_stream)
+                                         stream=self.cap_stream, level_offsets=self.offs)
         self.cap_stream.synchronize()
         self.flops = sum(flops_per_pair(lv.n) * int((self.lvl == k).sum()) for k, lv in enumerate(self.levels))
-        slices = -(-self.windows // 2048)  # the streaming schedule walks the batch in slices of 2048
-        self.launches_per_step = sum(1 if c == "fused" else 5 * slices for c in self.chosen)
+        # the streaming schedule walks each level's range in slices of 2048 windows
+        counts = [self.offs[k + 1] - self.offs[k] for k in range(len(self.levels))]
+        self.launches_per_step = (sum(1 if c == "fused" else 5 * -(-n // 2048)
+                                      for c, n in zip(self.chosen, counts) if c != "persistent")
+                                  + (1 if "persistent" in self.chosen else 0))
         self.h = [(torch.from_numpy(x[0]).pin_memory(), torch.from_numpy(x[1]).pin_memory()) for x in self.imgs]
         self.hout = torch.empty((self.windows, 8), dtype=torch.int32).pin_memory()
         self.config = {"windows_per_step": self.windows, "levels": [64, 128, 256],
@@ -656,14 +667,15 @@ class Whitening:
         self.out = torch.empty((self.windows, 8), dtype=torch.int32, device=dev)
         self.hout = torch.empty((self.windows, 8), dtype=torch.int32).pin_memory()
         self.flops = flops_per_pair(self.n) * self.windows
-        self.launches_per_step = 5 * E * -(-self.windows // 2048)
+        self.launches_per_step = 5 * E * -(-count // 2048)  # each exponent's range in slices of 2048
         self.count = count
         self.config = {"window": 256, "windows_per_step": self.windows, "pairs": count, "exponents": self.exps,
                        "input": "uint8"}
 
     def step(self, stream):
         E = len(self.exps)
-        self.plan.match([self.dref] * E, [self.dmov] * E, level=self.lvl, out=self.out, stream=stream)
+        self.plan.match([self.dref] * E, [self.dmov] * E, level=self.lvl, out=self.out, stream=stream,
+                        level_offsets=[self.count * e for e in range(E + 1)])
 
     def e2e_step(self, torch, stream):
         if not hasattr(self, "href"):
@@ -703,7 +715,7 @@ def make_workload(name, torch, swift, dev, args):
     if name == "noise64":
         return Noise64(torch, swift, dev)
     if name == "pyramid":
-        return Pyramid(torch, swift, dev)
+        return Pyramid(torch, swift, dev, schedule=args.schedule)
     if name in ("patches128", "patches256"):
         return Patches(torch, swift, dev, n=int(name[7:]), count=args.windows or 8192, precision=args.precision)
     if name == "warp":
@@ -1097,7 +1109,8 @@ def kernel_names(n: int) -> dict:
     (column pairs up to 256, per-column kernel at 512)."""
     return {"stats": "stream_stats_kernel", "rows": "stream_rows_kernel",
             "cols": "stream_cpair_kernel" if n <= 256 else "stream_cols_kernel",
-            "irows": "stream_irows_kernel", "final": "stream_peak_kernel", "fused": "swim_forward_kernel"}
+            "irows": "stream_irows_kernel", "final": "stream_peak_kernel", "fused": "swim_forward_kernel",
+            "persistent": "swim_persistent_kernel"}
 TC_KERNEL_NAMES = {"stats": "stream_stats_kernel", "rows": "tcf_rows_kernel", "cols": "tcf_cols_kernel",
                    "irows": "tcf_irows_kernel", "final": "stream_final_kernel"}
 
@@ -1112,6 +1125,8 @@ def main():
                     choices=["sections", "noise64", "pyramid", "patches128", "patches256", "warp", "whitening", "mir", "remod",
                              "align"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2", "fp16x2"])
+    ap.add_argument("--schedule", default="default", choices=["default", "fused", "stream", "persistent"],
+                    help="forward schedule of every level (FP32 workloads without their own choice)")
     ap.add_argument("--pairs", type=int, default=1, help="section pairs per step (sections workload)")
     ap.add_argument("--windows", type=int, default=0, help="limit the windows per step (small profiling cases)")
     ap.add_argument("--oracle-sample", type=int, default=961)
@@ -1141,6 +1156,10 @@ def main():
             dist.destroy_process_group()
         return
     W = make_workload(args.workload, torch, swift, dev, args)
+    if args.schedule != "default" and args.workload not in ("pyramid", "warp"):
+        for l in range(len(W.plan.levels)):
+            W.plan.set_schedule(l, args.schedule)
+        W.config["schedule"] = args.schedule
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     warm = max(args.warmup, 3)
@@ -1271,7 +1290,7 @@ def main():
                     **({"pipelining": "double-buffered: step k's host-to-device copy (copy stream) overlaps step "
                                       "k-1's match; every step copies its sections in and its results out"}
                        if hasattr(W, "e2e_run") else {})),
-        "gpu_launches": args.steps * W.launches_per_step,
+        "gpu_launches": args.steps * (sum(launches_per_step.values()) if launches_per_step else W.launches_per_step),
         "clocks": clocks,
     }
     if cpu is not None:

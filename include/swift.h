@@ -134,7 +134,16 @@ typedef struct {
  *                mir's affine triangles).  A window whose warped corners
  *                leave [0, h-1] x [0, w-1] is OUT_OF_BOUNDS.  The first call
  *                with warps (or the first backward) allocates the plan's
- *                extra workspace; make it before capturing the stream.      */
+ *                extra workspace; make it before capturing the stream.
+ *   level_offsets HOST int64 [n_levels + 1] or NULL.  When set, the windows
+ *                are sorted by level: level l's windows are b in
+ *                [level_offsets[l], level_offsets[l + 1]), with
+ *                level_offsets[0] = 0 and level_offsets[n_levels] = B
+ *                (non-decreasing).  Each level's launches then cover only
+ *                its own windows instead of scanning the whole batch for
+ *                them; `level` may be NULL (forward calls only: warped
+ *                windows and the backward need `level`).  A capture bakes
+ *                the offsets into the graph.                                 */
 typedef struct {
   const swift_image* ref;
   const swift_image* mov;
@@ -144,6 +153,7 @@ typedef struct {
   int64_t n_windows;
   int32_t patch_mode;
   const float* affine;
+  const int64_t* level_offsets;
 } swift_batch;
 
 /* Result of one window pair (32 bytes).
@@ -241,25 +251,55 @@ swift_status swift_match_batch_noalloc(const swift_level* level, swift_dtype in,
 swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, const float* grad_peak,
                                   const float* grad_snr, float* grad_affine, float* grad_w, void* stream);
 
-/* Forward schedules of a level.
- *   FUSED   one persistent kernel: each window's field lives in the shared
- *           memory of one CTA (64 x 64) or of a cluster of 2 (128 x 128) or
- *           8 (256 x 256) CTAs, with the row/column redistributions through
- *           distributed shared memory
- *   STREAM  five kernels of independent CTAs passing each window's
- *           intermediates through the plan's workspace
- *   DEFAULT FUSED for 64 x 64, STREAM for larger windows */
-typedef enum { SWIFT_SCHED_DEFAULT = 0, SWIFT_SCHED_FUSED = 1, SWIFT_SCHED_STREAM = 2 } swift_schedule;
+/* Forward schedules of a level (FP32 plans; the BF16X2 / FP16X2 forms have
+ * their own five-kernel schedule).
+ *   FUSED       one kernel per level: each window's field lives in the shared
+ *               memory of one CTA (64 x 64) or of a cluster of 2 (128 x 128)
+ *               or 8 (256 x 256) CTAs, with the row/column redistributions
+ *               through distributed shared memory
+ *   STREAM      five kernels per level (statistics, rows, column pairs,
+ *               inverse rows, finalize) of independent CTAs passing each
+ *               window's intermediates through the plan's workspace
+ *   PERSISTENT  the same five steps as work items of ONE kernel for every
+ *               level that has this schedule: CTAs claim items in a fixed
+ *               order from a queue and wait (bounded) for the items they
+ *               depend on; each window's intermediates live in a ring of
+ *               workspace slots small enough to stay in L2.  Windows of up to
+ *               256 x 256.  Results equal the STREAM schedule's bit for bit.
+ *               A wait that runs out (about 2 s) stops the launch's remaining
+ *               work: those windows report SWIFT_WIN_TIMEOUT.  The workspace
+ *               grows to the largest batch matched (a call that must grow it
+ *               may not be captured into a graph: swift_plan_capture makes an
+ *               uncaptured call first)
+ *   DEFAULT     PERSISTENT up to 256 x 256, STREAM for 512 x 512 */
+typedef enum {
+  SWIFT_SCHED_DEFAULT = 0,
+  SWIFT_SCHED_FUSED = 1,
+  SWIFT_SCHED_STREAM = 2,
+  SWIFT_SCHED_PERSISTENT = 3
+} swift_schedule;
 
 /* Choose the forward schedule of one level. */
 swift_status swift_plan_set_schedule(swift_plan plan, int32_t level, int32_t schedule);
 
-/* Autotuner: times every schedule of every level present in `batch` on this
- * batch (CUDA events; synchronises the host) and keeps the fastest for later
- * calls.  `chosen` (host int32 [n_levels], may be NULL) receives the picks.
- * On return `out` holds the batch's results under the chosen schedules. */
+/* Autotuner: on this batch (CUDA events; synchronises the host) it times
+ * the fused and streaming schedules of every level present, then the whole
+ * call with those per-level picks against one persistent launch of every
+ * level that has it, at each skew of the persistent work order (4, 8, 12,
+ * 16 windows between consecutive steps of a window: larger skews leave more
+ * items between a producer and its consumer, smaller ones keep a smaller
+ * ring in L2), and keeps the fastest for later calls.  `chosen` (host int32
+ * [n_levels], may be NULL) receives the schedule of each level.  On return
+ * `out` holds the batch's results under the chosen schedules. */
 swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swift_result* out, void* stream,
                                  int32_t* chosen);
+
+/* Skew of the persistent schedule's work order (1..16; default 16): stage k
+ * of a level's j-th window sits at time j + k * skew.  Larger skews leave
+ * more items between a producer and its consumer (fewer waits), smaller ones
+ * keep fewer windows in flight (a smaller ring of workspace slots, 5 * skew +
+ * 4, to hold in L2).  The autotuner sets it too. */
+swift_status swift_plan_set_skew(swift_plan plan, int32_t skew);
 
 /* Capture one forward call on `batch` (all its levels) into a CUDA graph
  * owned by the plan; swift_plan_replay then re-runs it with one graph
@@ -277,8 +317,8 @@ swift_status swift_plan_replay(swift_plan plan, void* stream);
  * starts over.  Slots: 0 statistics, 1 row transforms, 2 column
  * transforms + whitening, 3 inverse row transforms, 4 finalize (the
  * streaming schedule, and the same five kernels of the BF16X2 / FP16X2
- * forms), 5 fused kernel, 6-7 unused.  kernel_ms and launches are host
- * arrays of 8. */
+ * forms), 5 fused kernel, 6 persistent launch (its clearing of the work
+ * queue included), 7 unused.  kernel_ms and launches are host arrays of 8. */
 swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
 
 /* Test hook for the bounded-wait failure path (not for production use).
@@ -291,6 +331,16 @@ swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
  * uint8 windows, the fused schedule and the tensor-core forms do not use
  * this staging and are unaffected. */
 swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enable);
+
+/* Test hook for the persistent schedule's bounded waits (not for production
+ * use).  While `window` >= 0, the row-transform items of that window (its
+ * position in the launch's sequence of windows: the batch order for a batch
+ * without levels) never report completion, and every wait of the launch
+ * gives up after about 10 ms instead of 2 s.  The wait for that window's
+ * rows runs out, the launch stops its remaining work, and the windows not
+ * finished by then report SWIFT_WIN_TIMEOUT.  Nothing faults or hangs; the
+ * plan stays usable.  -1 turns the hook off. */
+swift_status swift_plan_set_test_hold(swift_plan plan, int64_t window);
 
 /* Test hook for the window guard (not for production use).  While enabled,
  * the statistics kernel of the FP32 streaming schedule reports windows of

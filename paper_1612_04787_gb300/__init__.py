@@ -20,11 +20,12 @@ import torch
 
 from . import _lib
 from ._lib import (APOD, DTYPE, PRECISION, SwiftBatch, SwiftImage, SwiftLevel, SwiftMesh, SwiftError,  # noqa: F401
-                   FIT_DEGENERATE, FIT_FALLBACK, FIT_OK, WIN_FLAT, WIN_NONFINITE, WIN_OK, WIN_OUT_OF_BOUNDS, check,
+                   FIT_DEGENERATE, FIT_FALLBACK, FIT_OK, WIN_FLAT, WIN_NONFINITE, WIN_OK, WIN_OUT_OF_BOUNDS, WIN_TIMEOUT,
+                   check,
                    lib)
 
 __all__ = ["Level", "Plan", "decode", "SwiftError", "version", "match_warped", "WIN_OK", "WIN_OUT_OF_BOUNDS",
-           "WIN_FLAT", "WIN_NONFINITE", "Mesh", "correspondences", "fit_affine", "mesh_fit", "render", "render_records", "downsample", "zmodel",
+           "WIN_FLAT", "WIN_NONFINITE", "WIN_TIMEOUT", "Mesh", "correspondences", "fit_affine", "mesh_fit", "render", "render_records", "downsample", "zmodel",
            "FIT_OK", "FIT_FALLBACK", "FIT_DEGENERATE"]
 
 
@@ -107,7 +108,7 @@ class Plan:
         check(lib.swift_plan_set_whitening(self._h, int(level), float(w)), "swift_plan_set_whitening")
         self.levels[level].whiten_exponent = float(w)
 
-    def _batch(self, ref, mov, ref_origin, mov_origin, level, affine):
+    def _batch(self, ref, mov, ref_origin, mov_origin, level, affine, level_offsets=None):
         patch = ref_origin is None and mov_origin is None
         refs = ref if isinstance(ref, (list, tuple)) else [ref]
         movs = mov if isinstance(mov, (list, tuple)) else [mov]
@@ -136,6 +137,12 @@ class Plan:
             if affine.dtype != torch.float32 or not affine.is_cuda or not affine.is_contiguous() \
                     or tuple(affine.shape) != (B, 6):
                 raise ValueError("affine must be a contiguous float32 [B, 6] CUDA tensor")
+        offs = None
+        if level_offsets is not None:
+            lo = [int(v) for v in level_offsets]
+            if len(lo) != nlv + 1 or lo[0] != 0 or lo[-1] != B or any(b < a for a, b in zip(lo, lo[1:])):
+                raise ValueError("level_offsets must be n_levels + 1 non-decreasing counts from 0 to B")
+            offs = (C.c_int64 * len(lo))(*lo)
         nl = len(refs)
         ri = (SwiftImage * nl)(*[_image(t, self.torch_dtype, patch) for t in refs])
         mi = (SwiftImage * nl)(*[_image(t, self.torch_dtype, patch) for t in movs])
@@ -144,17 +151,19 @@ class Plan:
                         None if patch else mov_origin.data_ptr(),
                         None if level is None else level.data_ptr(),
                         int(B), 1 if patch else 0,
-                        None if affine is None else affine.data_ptr())
-        return bt, (ri, mi), B, refs[0].device
+                        None if affine is None else affine.data_ptr(),
+                        offs)
+        return bt, (ri, mi, offs), B, refs[0].device
 
     def set_schedule(self, level: int, schedule: str):
         """Forward schedule of one level: "fused", "stream" or "default"."""
         check(lib.swift_plan_set_schedule(self._h, int(level), _lib.SCHEDULE[schedule]), "swift_plan_set_schedule")
 
-    def autotune(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None):
+    def autotune(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None,
+                 level_offsets=None):
         """Time every schedule of every level on this batch, keep the fastest;
         returns the chosen schedule names per level."""
-        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, None)
+        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, None, level_offsets)
         if out is None:
             out = torch.empty((B, 8), dtype=torch.int32, device=dev)
         chosen = (C.c_int32 * len(self.levels))()
@@ -163,9 +172,10 @@ class Plan:
         names = {v: k for k, v in _lib.SCHEDULE.items()}
         return [names[int(c)] for c in chosen], out
 
-    def capture(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None):
+    def capture(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None,
+                level_offsets=None):
         """Capture one forward call into a CUDA graph (see replay)."""
-        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, None)
+        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, None, level_offsets)
         if out is None:
             out = torch.empty((B, 8), dtype=torch.int32, device=dev)
         if stream is None:
@@ -174,12 +184,22 @@ class Plan:
               "swift_plan_capture")
         return out
 
-    KERNEL_SLOTS = ("stats", "rows", "cols", "irows", "final", "fused")
+    KERNEL_SLOTS = ("stats", "rows", "cols", "irows", "final", "fused", "persistent")
 
     def set_test_stall(self, enable: bool):
         """Test hook: float32 row staging waits for bytes that never arrive,
         so its bounded wait runs out and windows report status 4 (timeout)."""
         check(lib.swift_plan_set_test_stall(self._h, 1 if enable else 0), "swift_plan_set_test_stall")
+
+    def set_skew(self, skew: int):
+        """Skew (1..16) of the persistent schedule's work order."""
+        check(lib.swift_plan_set_skew(self._h, int(skew)), "swift_plan_set_skew")
+
+    def set_test_hold(self, window: int):
+        """Test hook: the row items of ``window`` (its position in the
+        persistent launch's window sequence) never report completion and the
+        launch's waits give up after about 10 ms; -1 turns it off."""
+        check(lib.swift_plan_set_test_hold(self._h, int(window)), "swift_plan_set_test_hold")
 
     def set_test_stale_status(self, enable: bool):
         """Test hook: the statistics kernel reports windows of other levels as
@@ -218,7 +238,8 @@ class Plan:
                                        g_w.data_ptr(), _stream_ptr(stream)), "swift_match_backward")
         return g_aff, g_w
 
-    def match(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None, affine=None):
+    def match(self, ref, mov, ref_origin=None, mov_origin=None, level=None, out=None, stream=None, affine=None,
+              level_offsets=None):
         """Forward match; returns ``out`` ([B, 8] int32 device tensor of results).
 
         Section mode: ``ref`` / ``mov`` are [H, W] uint8/float32 images (``ref``
@@ -227,8 +248,11 @@ class Plan:
         int32 [B, 2] (y, x) device tensors.  Patch mode (no origins): ``ref``
         and ``mov`` are [B, n, n] stacks.  ``affine`` ([B, 6] float32, section
         mode) resamples each moving window bilinearly under its warp.
+        ``level_offsets`` (n_levels + 1 ints): the windows are sorted by
+        level, level l's being [level_offsets[l], level_offsets[l + 1]); each
+        level's launches then cover only its own windows.
         """
-        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, affine)
+        bt, keep, B, dev = self._batch(ref, mov, ref_origin, mov_origin, level, affine, level_offsets)
         if out is None:
             out = torch.empty((B, 8), dtype=torch.int32, device=dev)
         elif out.dtype != torch.int32 or out.shape != (B, 8) or not out.is_contiguous():
@@ -305,7 +329,7 @@ def whitening_sweep(ref, mov, n: int, exponents, apod: str = "hann", tukey_alpha
     rr = ref.unsqueeze(0).expand(E, P, n, n).reshape(E * P, n, n).contiguous()
     mm = mov.unsqueeze(0).expand(E, P, n, n).reshape(E * P, n, n).contiguous()
     lvl = torch.arange(E, dtype=torch.int32, device=ref.device).repeat_interleave(P)
-    out = plan.match([rr] * E, [mm] * E, level=lvl, stream=stream)
+    out = plan.match([rr] * E, [mm] * E, level=lvl, stream=stream, level_offsets=[P * e for e in range(E + 1)])
     return out.view(E, P, 8)
 
 

@@ -23,9 +23,9 @@ SWIFT_ERR_CAPACITY = 6
 APOD = {"none": 0, "hann": 1, "tukey": 2}
 DTYPE = {"u8": 0, "f32": 1}
 PRECISION = {"fp32": 0, "bf16x2": 1, "fp16x2": 2}
-SCHEDULE = {"default": 0, "fused": 1, "stream": 2}
+SCHEDULE = {"default": 0, "fused": 1, "stream": 2, "persistent": 3}
 
-WIN_OK, WIN_OUT_OF_BOUNDS, WIN_FLAT, WIN_NONFINITE = 0, 1, 2, 3
+WIN_OK, WIN_OUT_OF_BOUNDS, WIN_FLAT, WIN_NONFINITE, WIN_TIMEOUT = 0, 1, 2, 3, 4
 
 # every symbol include/swift.h declares
 EXPORTS = (
@@ -41,6 +41,8 @@ EXPORTS = (
     "swift_plan_replay",
     "swift_plan_set_timing",
     "swift_plan_set_test_stall",
+    "swift_plan_set_test_hold",
+    "swift_plan_set_skew",
     "swift_plan_set_test_stale_status",
     "swift_window_check",
     "swift_plan_timings",
@@ -72,7 +74,8 @@ class SwiftImage(C.Structure):
 class SwiftBatch(C.Structure):
     _fields_ = [("ref", C.POINTER(SwiftImage)), ("mov", C.POINTER(SwiftImage)),
                 ("ref_origin", C.c_void_p), ("mov_origin", C.c_void_p), ("level", C.c_void_p),
-                ("n_windows", C.c_int64), ("patch_mode", C.c_int32), ("affine", C.c_void_p)]
+                ("n_windows", C.c_int64), ("patch_mode", C.c_int32), ("affine", C.c_void_p),
+                ("level_offsets", C.POINTER(C.c_int64))]
 
 
 class SwiftResult(C.Structure):
@@ -122,6 +125,10 @@ def _load():
     lib.swift_plan_set_timing.restype = C.c_int
     lib.swift_plan_set_test_stall.argtypes = [C.c_void_p, C.c_int32]
     lib.swift_plan_set_test_stall.restype = C.c_int
+    lib.swift_plan_set_test_hold.argtypes = [C.c_void_p, C.c_int64]
+    lib.swift_plan_set_test_hold.restype = C.c_int
+    lib.swift_plan_set_skew.argtypes = [C.c_void_p, C.c_int32]
+    lib.swift_plan_set_skew.restype = C.c_int
     lib.swift_plan_set_test_stale_status.argtypes = [C.c_void_p, C.c_int32]
     lib.swift_plan_set_test_stale_status.restype = C.c_int
     lib.swift_window_check.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32),

@@ -43,14 +43,22 @@ struct swift_plan_s {
   float2* twiddle[kNumSizes] = {};
   // tensor-core precision variant: fragment and twiddle tables per window size
   void* tc_tab[kNumSizes] = {};
-  // streaming forward path: per-level choice and its workspace
-  int stream_level[kMaxLevels] = {};
+  // forward schedule of each level (SWIFT_SCHED_FUSED / _STREAM / _PERSISTENT)
+  int sched[kMaxLevels] = {};
+  // streaming forward path: its workspace
   void* work = nullptr;
   long long work_windows = 0;  // capacity (windows of the largest streamed size)
   // affine-warp forward and backward: allocated on first use
   void* bwork = nullptr;
   long long bwork_windows = 0;
   double* gw_acc = nullptr;  // [kMaxLevels] accumulated dL/dw
+  // persistent schedule: workspace (grown to the largest batch seen), skew
+  // and ring of its work order, the bound of its waits, and its test hook
+  void* pwork = nullptr;
+  size_t pwork_bytes = 0;
+  int pskew = 16;
+  long long pspin = 4000000000ll;  // clock cycles (about 2 s at 2 GHz)
+  long long phold = -1;            // swift_plan_set_test_hold
   // per-kernel timing (swift_plan_set_timing / swift_plan_timings): a ring
   // of event sets, one set per streaming slice or fused launch
   bool test_stall = false;  // swift_plan_set_test_stall
@@ -79,7 +87,14 @@ constexpr long long kStreamSlice = SWIFT_STREAM_SLICE;
 constexpr long long kBackSlice = 1024;
 // default forward schedule: 128 x 128 and larger windows stream their
 // intermediates through the workspace; 64 x 64 windows use the fused kernel
-bool default_stream(int n) { return n >= 128; }
+// (the persistent one-launch schedule measured slower on every workload)
+int default_sched(int n) { return n >= 128 ? SWIFT_SCHED_STREAM : SWIFT_SCHED_FUSED; }
+bool has_persistent(int n) { return n == 64 || n == 128 || n == 256; }
+// ring slots of the persistent schedule for skew D (RING > 4 D); skews tried
+// by the autotuner
+int persist_ring(int skew) { return 5 * skew + 4; }
+constexpr int kMaxSkew = 16;
+constexpr int kSkews[] = {4, 8, 12, 16};
 }  // namespace
 
 static swift_status release(swift_plan p) {
@@ -95,6 +110,7 @@ static swift_status release(swift_plan p) {
   }
   if (p->work) cudaFree(p->work);
   if (p->bwork) cudaFree(p->bwork);
+  if (p->pwork) cudaFree(p->pwork);
   if (p->tev) {
     for (int i = 0; i < 6 * kTimingSets; ++i) cudaEventDestroy(p->tev[i]);
     delete[] p->tev;
@@ -188,7 +204,7 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
   // sized for the largest level, so any level can be switched to streaming
   size_t per = 0;
   for (int l = 0; l < n_levels; ++l) {
-    p->stream_level[l] = default_stream(levels[l].n) ? 1 : 0;
+    p->sched[l] = default_sched(levels[l].n);
     const size_t b = swift::stream_bytes_per_window(levels[l].n);
     per = b > per ? b : per;
   }
@@ -206,6 +222,24 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
 
 extern "C" swift_status swift_plan_destroy(swift_plan plan) { return release(plan); }
 
+// levels a batch uses: all of the plan's when it carries a level array or
+// level offsets, else level 0 only
+static int batch_levels(swift_plan plan, const swift_batch* batch) {
+  return (batch->level || batch->level_offsets) ? plan->n_levels : 1;
+}
+
+// window range [*b0, *b0 + *cnt) of level l: the whole batch, or the level's
+// range of a batch sorted by level
+static void level_range(const swift_batch* batch, int l, int64_t* b0, int64_t* cnt) {
+  if (batch->level_offsets) {
+    *b0 = batch->level_offsets[l];
+    *cnt = batch->level_offsets[l + 1] - batch->level_offsets[l];
+  } else {
+    *b0 = 0;
+    *cnt = batch->n_windows;
+  }
+}
+
 static bool image_ok(const swift_image& im, int n, int patch_mode, int64_t B) {
   if (!im.data || im.count < 1) return false;
   if (patch_mode) {
@@ -217,8 +251,8 @@ static bool image_ok(const swift_image& im, int n, int patch_mode, int64_t B) {
   return true;
 }
 
-// Launch the windows of level l with the level's schedule (fused or streaming).
-static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, swift_result* out, cudaStream_t st) {
+// Launch description of level l of a forward batch (section or patch mode).
+static swift::MatchLaunch level_launch_forward(swift_plan plan, const swift_batch* batch, int l, swift_result* out) {
   const int64_t B = batch->n_windows;
   const int pm = batch->patch_mode ? 1 : 0;
   const swift_level& lv = plan->levels[l];
@@ -251,6 +285,35 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
   L.stall_tx = plan->test_stall ? 16u : 0u;
   L.stale_ok = plan->test_stale_ok ? 1 : 0;
   L.out = out;
+  if (batch->level_offsets) {
+    // a batch sorted by level: this level's windows only, as a batch of their own
+    int64_t b0 = 0, cnt = 0;
+    level_range(batch, l, &b0, &cnt);
+    const size_t es = plan->dtype == SWIFT_IN_U8 ? 1 : 4;
+    if (pm) {
+      L.ref = static_cast<const unsigned char*>(L.ref) + es * b0 * L.ref_stride;
+      L.mov = static_cast<const unsigned char*>(L.mov) + es * b0 * L.mov_stride;
+    } else {
+      L.ref_origin += 2 * b0;
+      L.mov_origin += 2 * b0;
+    }
+    L.out = out ? out + b0 : nullptr;
+    L.level_idx = nullptr;
+    L.n_windows = cnt;
+  }
+  return L;
+}
+
+// Launch the windows of level l with the level's schedule (fused or streaming).
+static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, swift_result* out, cudaStream_t st) {
+  int64_t B0 = 0, B = 0;
+  level_range(batch, l, &B0, &B);
+  if (B == 0) return SWIFT_OK;
+  const int pm = batch->patch_mode ? 1 : 0;
+  const swift_level& lv = plan->levels[l];
+  const swift_image& ri = batch->ref[l];
+  const swift_image& mi = batch->mov[l];
+  const swift::MatchLaunch L = level_launch_forward(plan, batch, l, out);
   if (plan->prec != SWIFT_PREC_FP32) {
     const bool fp16 = plan->prec == SWIFT_PREC_FP16X2;
     for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
@@ -266,7 +329,7 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
     }
     return SWIFT_OK;
   }
-  if (plan->stream_level[l]) {
+  if (plan->sched[l] != SWIFT_SCHED_FUSED) {
     for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
       const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
       swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
@@ -327,12 +390,82 @@ static void order_end(swift_plan p, cudaStream_t st, bool captured) {
   }
 }
 
+// The levels of the batch with the persistent schedule, all in one launch.
+static swift_status run_persistent(swift_plan plan, const swift_batch* batch, unsigned int mask, swift_result* out,
+                                   cudaStream_t st) {
+  const int64_t B = batch->n_windows;
+  const int used_levels = batch_levels(plan, batch);
+  swift::PersistLaunch P = {};
+  P.n_levels = used_levels;
+  P.level_mask = mask;
+  P.B = B;
+  P.level_idx = batch->level_offsets ? nullptr : batch->level;
+  P.sorted = batch->level_offsets ? 1 : 0;
+  for (int l = 0; l <= used_levels && batch->level_offsets; ++l) P.level_off[l] = batch->level_offsets[l];
+  P.skew = plan->pskew;
+  P.ring = persist_ring(plan->pskew);
+  P.spin_limit = plan->phold >= 0 ? 20000000ll : plan->pspin;  // the test hook waits about 10 ms
+  P.hold_s1 = plan->phold;
+  P.nmax = 0;
+  for (int l = 0; l < used_levels; ++l) {
+    if (!((mask >> l) & 1u)) continue;
+    swift_batch whole = *batch;
+    whole.level_offsets = nullptr;  // the persistent kernel indexes the whole batch itself
+    P.lv[l].L = level_launch_forward(plan, &whole, l, out);
+    P.lv[l].n = plan->levels[l].n;
+    P.nmax = plan->levels[l].n > P.nmax ? plan->levels[l].n : P.nmax;
+  }
+  for (int l = 0; l < used_levels; ++l)
+    if (!((mask >> l) & 1u)) P.lv[l].n = P.nmax;  // not run: any built size
+  // workspace, grown to the largest batch and ring seen (before any capture:
+  // swift_plan_capture makes an uncaptured call first)
+  const size_t need = swift::persist_bytes(used_levels, B, 256, persist_ring(kMaxSkew));
+  if (need > plan->pwork_bytes) {
+    bool captured = false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess) captured = cs != cudaStreamCaptureStatusNone;
+    if (captured) return SWIFT_ERR_INVALID_ARG;  // a capture needs the same batch size as the call before it
+    if (plan->pwork) {
+      cudaStreamSynchronize(st);
+      cudaFree(plan->pwork);
+      plan->pwork = nullptr;
+      plan->pwork_bytes = 0;
+    }
+    if (cudaMalloc(&plan->pwork, need) != cudaSuccess) {
+      plan->pwork = nullptr;
+      cudaGetLastError();
+      return SWIFT_ERR_OOM;
+    }
+    plan->pwork_bytes = need;
+  }
+  cudaEvent_t* ev = nullptr;
+  if (plan->timing) {
+    const int set = plan->tcount++ % kTimingSets;
+    plan->tkind[set] = 2;
+    ev = plan->tev + 6 * set;
+    cudaEventRecord(ev[0], st);
+  }
+  if (swift::launch_persist(P, plan->pwork, plan->dtype, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+  if (ev) cudaEventRecord(ev[1], st);
+  return SWIFT_OK;
+}
+
 // the launches of one validated forward call
 static swift_status match_launches(swift_plan plan, const swift_batch* batch, swift_result* out, cudaStream_t st) {
   if (batch->affine) return warp_forward(plan, batch, out, st);
-  const int used_levels = batch->level ? plan->n_levels : 1;
+  const int used_levels = batch_levels(plan, batch);
+  unsigned int mask = 0;
   for (int l = 0; l < used_levels; ++l) {
+    if (plan->prec == SWIFT_PREC_FP32 && plan->sched[l] == SWIFT_SCHED_PERSISTENT && has_persistent(plan->levels[l].n) &&
+        batch->n_windows < (1ll << 24)) {
+      mask |= 1u << l;
+      continue;
+    }
     const swift_status e = run_level(plan, batch, l, out, st);
+    if (e != SWIFT_OK) return e;
+  }
+  if (mask) {
+    const swift_status e = run_persistent(plan, batch, mask, out, st);
     if (e != SWIFT_OK) return e;
   }
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
@@ -349,11 +482,17 @@ extern "C" swift_status swift_match_batch(swift_plan plan, const swift_batch* ba
   if (B * 4 > static_cast<int64_t>(0x7fffffff)) return SWIFT_ERR_INVALID_ARG;  // grid limit
   const int pm = batch->patch_mode ? 1 : 0;
   if (!pm && (!batch->ref_origin || !batch->mov_origin)) return SWIFT_ERR_INVALID_ARG;
-  const int used_levels = batch->level ? plan->n_levels : 1;
+  const int used_levels = batch_levels(plan, batch);
   for (int l = 0; l < used_levels; ++l) {
     const int n = plan->levels[l].n;
     if (!image_ok(batch->ref[l], n, pm, B) || !image_ok(batch->mov[l], n, pm, B)) return SWIFT_ERR_INVALID_ARG;
     if (batch->mov[l].count != 1) return SWIFT_ERR_INVALID_ARG;
+  }
+  if (batch->level_offsets) {
+    const int64_t* o = batch->level_offsets;
+    if (o[0] != 0 || o[plan->n_levels] != B) return SWIFT_ERR_INVALID_ARG;
+    for (int l = 0; l < plan->n_levels; ++l)
+      if (o[l + 1] < o[l]) return SWIFT_ERR_INVALID_ARG;
   }
   // report (and clear) an asynchronous failure left by earlier work
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
@@ -441,6 +580,7 @@ static swift_status check_warp_batch(swift_plan plan, const swift_batch* batch) 
   if (B == 0) return SWIFT_OK;
   if (batch->patch_mode || !batch->ref || !batch->mov || !batch->ref_origin || !batch->mov_origin)
     return SWIFT_ERR_INVALID_ARG;
+  if (batch->level_offsets && !batch->level) return SWIFT_ERR_UNSUPPORTED;  // warped windows need the level array
   const int used = batch->level ? plan->n_levels : 1;
   for (int l = 0; l < used; ++l) {
     if (!image_ok(batch->ref[l], plan->levels[l].n, 0, B) || !image_ok(batch->mov[l], plan->levels[l].n, 0, B))
@@ -515,14 +655,29 @@ static swift_status backward_launches(swift_plan plan, const swift_batch* batch,
 
 extern "C" swift_status swift_plan_set_schedule(swift_plan plan, int32_t level, int32_t schedule) {
   if (!plan || level < 0 || level >= plan->n_levels) return SWIFT_ERR_INVALID_ARG;
+  const int n = plan->levels[level].n;
   if (schedule == SWIFT_SCHED_DEFAULT) {
-    plan->stream_level[level] = default_stream(plan->levels[level].n) ? 1 : 0;
-  } else if (schedule == SWIFT_SCHED_FUSED || schedule == SWIFT_SCHED_STREAM) {
-    if (schedule == SWIFT_SCHED_FUSED && !has_fused(plan->levels[level].n)) return SWIFT_ERR_UNSUPPORTED;
-    plan->stream_level[level] = schedule == SWIFT_SCHED_STREAM ? 1 : 0;
+    plan->sched[level] = default_sched(n);
+  } else if (schedule == SWIFT_SCHED_FUSED || schedule == SWIFT_SCHED_STREAM || schedule == SWIFT_SCHED_PERSISTENT) {
+    if (schedule == SWIFT_SCHED_FUSED && !has_fused(n)) return SWIFT_ERR_UNSUPPORTED;
+    if (schedule == SWIFT_SCHED_PERSISTENT && !has_persistent(n)) return SWIFT_ERR_UNSUPPORTED;
+    plan->sched[level] = schedule;
   } else {
     return SWIFT_ERR_INVALID_ARG;
   }
+  return SWIFT_OK;
+}
+
+// time `reps` forward calls of the batch on `st` (after one warm-up call)
+static swift_status time_calls(swift_plan plan, const swift_batch* batch, swift_result* out, cudaStream_t st,
+                               cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  swift_status e = match_launches(plan, batch, out, st);  // warm-up
+  if (e != SWIFT_OK) return e;
+  cudaEventRecord(e0, st);
+  for (int rep = 0; rep < 3 && e == SWIFT_OK; ++rep) e = match_launches(plan, batch, out, st);
+  cudaEventRecord(e1, st);
+  if (e != SWIFT_OK) return e;
+  if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) return SWIFT_ERR_CUDA;
   return SWIFT_OK;
 }
 
@@ -530,7 +685,7 @@ extern "C" swift_status swift_plan_autotune(swift_plan plan, const swift_batch* 
                                             void* stream, int32_t* chosen) {
   if (!plan || !batch) return SWIFT_ERR_INVALID_ARG;
   if (batch->affine) return SWIFT_ERR_INVALID_ARG;
-  // run once with the current schedules: validates the batch and warms up
+  // run once with the current schedules: validates the batch and does the set-up
   swift_status e = swift_match_batch(plan, batch, out, stream);
   if (e != SWIFT_OK) return e;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -540,30 +695,59 @@ extern "C" swift_status swift_plan_autotune(swift_plan plan, const swift_batch* 
     cudaGetLastError();
     return SWIFT_ERR_CUDA;
   }
-  const int used = batch->level ? plan->n_levels : 1;
-  e = SWIFT_OK;
+  const int used = batch_levels(plan, batch);
+  // (a) per level: the faster of the fused and streaming schedules, each
+  // level timed alone
+  int per_level[kMaxLevels];
   for (int l = 0; l < used && e == SWIFT_OK; ++l) {
     float best = 3.4e38f;
-    int best_sched = plan->stream_level[l];
-    for (int sched = has_fused(plan->levels[l].n) ? 0 : 1; sched < 2 && e == SWIFT_OK; ++sched) {
-      plan->stream_level[l] = sched;
+    per_level[l] = SWIFT_SCHED_STREAM;
+    for (int s : {SWIFT_SCHED_FUSED, SWIFT_SCHED_STREAM}) {
+      if (s == SWIFT_SCHED_FUSED && !has_fused(plan->levels[l].n)) continue;
+      plan->sched[l] = s;
       if ((e = run_level(plan, batch, l, out, st)) != SWIFT_OK) break;  // warm-up
       cudaEventRecord(e0, st);
       for (int rep = 0; rep < 3 && e == SWIFT_OK; ++rep) e = run_level(plan, batch, l, out, st);
       cudaEventRecord(e1, st);
       float ms = 0.f;
+      if (e != SWIFT_OK) break;
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
         e = SWIFT_ERR_CUDA;
         break;
       }
       if (ms < best) {
         best = ms;
-        best_sched = sched;
+        per_level[l] = s;
       }
     }
-    plan->stream_level[l] = best_sched;
-    if (chosen) chosen[l] = best_sched ? SWIFT_SCHED_STREAM : SWIFT_SCHED_FUSED;
   }
+  float best_ms = 3.4e38f;
+  int best_skew = plan->pskew;
+  bool best_persist = false;
+  if (e == SWIFT_OK) {
+    for (int l = 0; l < used; ++l) plan->sched[l] = per_level[l];
+    e = time_calls(plan, batch, out, st, e0, e1, &best_ms);
+  }
+  // (b) every level that has it in one persistent launch, for each skew of
+  // its work order (ring and L2 working set grow with the skew)
+  bool any = false;
+  for (int l = 0; l < used; ++l) any = any || (plan->prec == SWIFT_PREC_FP32 && has_persistent(plan->levels[l].n));
+  for (int k = 0; any && e == SWIFT_OK && k < static_cast<int>(sizeof(kSkews) / sizeof(kSkews[0])); ++k) {
+    for (int l = 0; l < used; ++l) plan->sched[l] = has_persistent(plan->levels[l].n) ? SWIFT_SCHED_PERSISTENT : per_level[l];
+    plan->pskew = kSkews[k];
+    float ms = 0.f;
+    if ((e = time_calls(plan, batch, out, st, e0, e1, &ms)) != SWIFT_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_skew = kSkews[k];
+      best_persist = true;
+    }
+  }
+  for (int l = 0; l < used; ++l)
+    plan->sched[l] = best_persist && has_persistent(plan->levels[l].n) ? SWIFT_SCHED_PERSISTENT : per_level[l];
+  plan->pskew = best_skew;
+  if (chosen)
+    for (int l = 0; l < used; ++l) chosen[l] = plan->sched[l];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != SWIFT_OK) return e;
@@ -624,6 +808,18 @@ extern "C" swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enabl
   return SWIFT_OK;
 }
 
+extern "C" swift_status swift_plan_set_skew(swift_plan plan, int32_t skew) {
+  if (!plan || skew < 1 || skew > kMaxSkew) return SWIFT_ERR_INVALID_ARG;
+  plan->pskew = skew;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_test_hold(swift_plan plan, int64_t window) {
+  if (!plan || window < -1) return SWIFT_ERR_INVALID_ARG;
+  plan->phold = window;
+  return SWIFT_OK;
+}
+
 extern "C" swift_status swift_plan_set_test_stale_status(swift_plan plan, int32_t enable) {
   if (!plan) return SWIFT_ERR_INVALID_ARG;
   plan->test_stale_ok = enable != 0;
@@ -677,12 +873,12 @@ extern "C" swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, in
   const int used = plan->tcount < kTimingSets ? plan->tcount : kTimingSets;
   for (int set = 0; set < used; ++set) {
     cudaEvent_t* ev = plan->tev + 6 * set;
-    const int nk = plan->tkind[set] == 0 ? 5 : 1;
+    const int nk = plan->tkind[set] == 0 ? 5 : 1;  // 1: fused launch, 2: persistent launch
     if (cudaEventSynchronize(ev[nk]) != cudaSuccess) return SWIFT_ERR_CUDA;
     for (int k = 0; k < nk; ++k) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return SWIFT_ERR_CUDA;
-      const int slot = plan->tkind[set] == 0 ? k : 5;
+      const int slot = plan->tkind[set] == 0 ? k : (plan->tkind[set] == 1 ? 5 : 6);
       kernel_ms[slot] += ms;
       launches[slot] += 1;
     }

@@ -143,6 +143,46 @@ TcfLaunch tcf_tables(const void* dst);
 cudaError_t launch_tcf(int n, swift_dtype dtype, bool fp16, const MatchLaunch& L, const StreamWork& W,
                        const TcfLaunch& T, cudaStream_t stream);
 
+// persistent forward schedule (swim_persist.cu): every window of the levels
+// in one launch; bytes of its workspace, and the launch (the launch
+// description's workspace pointers are filled in from `work`)
+constexpr int kPersistMaxLevels = 16;
+constexpr int kPersistStages = 5;
+constexpr int kPersistPartStride = 24;  // u64 partials per window (NB3 <= 8, three each)
+constexpr int kCompactWindows = 2048;   // windows per compaction item
+struct PersistLevel {
+  MatchLaunch L;  // the level's launch (tables, images, origins, results)
+  int n;          // window side (64, 128, 256)
+};
+
+struct PersistLaunch {
+  PersistLevel lv[kPersistMaxLevels];
+  int n_levels;
+  int ring, skew;                // RING slots (shared by the levels), skew D (RING > 4 D)
+  long long B;                   // windows in the batch
+  const int* level_idx;          // [B] or null (every window is level 0)
+  unsigned int level_mask;       // levels run by this launch (bit l)
+  int sorted;                    // windows sorted by level: level l is [level_off[l], level_off[l + 1])
+  long long level_off[kPersistMaxLevels + 1];
+  int* lists;                    // [n_levels][B] window indices per level
+  unsigned int* lcount;          // [kPersistMaxLevels] windows per level
+  float4* stats;                 // [B]
+  unsigned long long* part;      // [B][kPersistPartStride]
+  float2* zr;                    // ring [RING][nmax][nmax] row spectra
+  float2* h;                     // ring [RING][nmax][nmax/2] inverse-column output
+  int nmax;                      // largest window side of the launch
+  unsigned long long* slot;      // [RING] tag (bits 40-63: window + 1) and per-stage counts (8 bits each)
+  unsigned int* queue;           // next item
+  unsigned int* comp_done;       // compaction items done
+  unsigned int* abort;           // nonzero once a wait ran out
+  int n_compact;                 // compaction items (0 without a level array)
+  long long spin_limit;          // clock cycles a wait may take
+  long long hold_s1;             // test hook: window (sequence position) whose S1 items never signal, or -1
+};
+
+size_t persist_bytes(int n_levels, long long B, int nmax, int ring);
+cudaError_t launch_persist(PersistLaunch P, void* work, swift_dtype dtype, cudaStream_t stream);
+
 // float32 copy of the accumulated dL/dw of n levels
 cudaError_t launch_wout(const double* acc, float* out, int n, cudaStream_t stream);
 

@@ -65,23 +65,51 @@ struct StreamGeom {
 
 __device__ __forceinline__ int stat_status(const float4& s) { return __float_as_int(s.z); }
 
+// One window's view of a workspace: batch index (origins, level, result) and
+// its own statistics word, row spectra Zr, inverse-column output H and K3
+// block partials.  The five-kernel schedule takes window s of a slice; the
+// persistent schedule takes a ring slot.  Workspace words are read through
+// L2 (ld.global.cg): in the persistent schedule another SM may have written
+// them since this SM's L1 last saw those lines.
+struct WinRef {
+  long long b;               // window index in the batch
+  float4* stats;             // [1]
+  float2* zr;                // [n][n]
+  float2* h;                 // [n][n/2]
+  unsigned long long* part;  // [NB3][3]
+  const int* pre;            // status decided before the statistics, or null
+};
+
+template <int N>
+__device__ __forceinline__ WinRef slice_ref(const MatchLaunch& L, const StreamWork& W, long long s) {
+  WinRef R;
+  R.b = W.b0 + s;
+  R.stats = W.stats + s;
+  R.zr = W.zr + s * N * N;
+  R.h = W.h + s * N * (N / 2);
+  R.part = W.part + 3 * s * StreamGeom<N>::NB3;
+  R.pre = L.pre_status != nullptr ? L.pre_status + s : nullptr;
+  return R;
+}
+
+__device__ __forceinline__ float4 load_stats(const WinRef& R) { return __ldcg(R.stats); }
+
 // ---------------------------------------------------------------------------
 // K0: statistics
 // ---------------------------------------------------------------------------
 template <int N, typename TIn>
-__global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, const StreamWork W) {
-  const long long s = blockIdx.x;
-  const long long b = W.b0 + s;
+__device__ __forceinline__ void stats_stage(const MatchLaunch& L, const WinRef& R) {
+  const long long b = R.b;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ float tap[N];
   __shared__ double red[8][2];
   __shared__ float mred[8][4];
   __shared__ int bred[8];
   auto put = [&](int status, float mm, float mr) {
-    if (tid == 0) W.stats[s] = make_float4(mm, mr, __int_as_float(status), 0.f);
+    if (tid == 0) *R.stats = make_float4(mm, mr, __int_as_float(status), 0.f);
   };
-  if (L.pre_status != nullptr && L.pre_status[s] != SWIFT_WIN_OK) {
-    put(L.pre_status[s], 0.f, 0.f);
+  if (R.pre != nullptr && *R.pre != SWIFT_WIN_OK) {
+    put(*R.pre, 0.f, 0.f);
     return;
   }
   const int guard = launch_window_check(L, b, N);
@@ -207,9 +235,14 @@ __global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, 
       nb |= bred[v];
     }
     const int st = nb ? SWIFT_WIN_NONFINITE : ((e == f || g == h) ? SWIFT_WIN_FLAT : SWIFT_WIN_OK);
-    W.stats[s] = make_float4(static_cast<float>(tm * L.inv_sum_a), static_cast<float>(tr * L.inv_sum_a),
-                             __int_as_float(st), 0.f);
+    *R.stats = make_float4(static_cast<float>(tm * L.inv_sum_a), static_cast<float>(tr * L.inv_sum_a),
+                           __int_as_float(st), 0.f);
   }
+}
+
+template <int N, typename TIn>
+__global__ void __launch_bounds__(256) stream_stats_kernel(const MatchLaunch L, const StreamWork W) {
+  stats_stage<N, TIn>(L, slice_ref<N>(L, W, blockIdx.x));
 }
 
 // ---------------------------------------------------------------------------
@@ -275,7 +308,7 @@ __device__ __forceinline__ void transpose16_u8(uint32_t (&w)[4], int L) {
 }
 
 template <int N, typename TIn>
-__global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, const StreamWork W) {
+__device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R, int rb) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, RB = G::RB, RS = G::RS, T = G::T;
   constexpr int KB = (RB * R1 + T - 1) / T;
@@ -284,18 +317,16 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
   // uint8 windows of 256 x 256: pass A takes its pixels from the thread's own
   // 16-byte loads through a half-warp byte transpose instead of a staged copy
   constexpr bool kShfl = N == 256 && sizeof(TIn) == 1;
-  const long long s = blockIdx.x / (N / RB);
-  const int rb = blockIdx.x % (N / RB);
-  const long long b = W.b0 + s;
+  const long long b = R.b;
   const int tid = threadIdx.x;
-  const float4 st = W.stats[s];
+  const float4 st = load_stats(R);
   if (stat_status(st) != SWIFT_WIN_OK) return;
   {
     // the window's level and bounds, from the launch's own arrays: a status
     // word left by another call never makes this kernel read
     const int guard = launch_window_check(L, b, N);
     if (guard != SWIFT_WIN_OK) {
-      if (tid == 0) W.stats[s] = make_float4(0.f, 0.f, __int_as_float(guard), 0.f);
+      if (tid == 0) *R.stats = make_float4(0.f, 0.f, __int_as_float(guard), 0.f);
       return;
     }
   }
@@ -371,7 +402,7 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
       if (__syncthreads_or(!arrived)) {
         if (tid == 0) {
           mbar_wait_bounded(mbar, 0);
-          W.stats[s] = make_float4(0.f, 0.f, __int_as_float(SWIFT_WIN_TIMEOUT), 0.f);
+          *R.stats = make_float4(0.f, 0.f, __int_as_float(SWIFT_WIN_TIMEOUT), 0.f);
         }
         return;
       }
@@ -468,10 +499,16 @@ __global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, c
       v[n2] = n2 == 0 ? x : cmul(x, twid[n2 * R1 + k1]);
     }
     dft<R2, -1>(v);
-    float2* zrow = W.zr + (s * N + rb * RB + ln) * N;
+    float2* zrow = R.zr + (rb * RB + ln) * N;
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) zrow[k1 + R1 * k2] = v[k2];
   }
+}
+
+template <int N, typename TIn>
+__global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, const StreamWork W) {
+  constexpr int NRB = N / StreamGeom<N>::RB;
+  rows_stage<N, TIn>(L, slice_ref<N>(L, W, blockIdx.x / NRB), blockIdx.x % NRB);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,14 +720,12 @@ __device__ __forceinline__ float whiten_scaled(float mag2, float half_w, float l
 }
 
 template <int N>
-__global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch L, const StreamWork W) {
+__device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& R, int cb) {
   using P = PairGeom<N>;
   constexpr int R1 = P::R1, R2 = P::R2, CB = P::CB, T = P::T, TW = P::TW;
   constexpr int RB = P::TB / T;  // pass B rounds per thread
-  const long long s = blockIdx.x / P::NB;
-  const int cb = blockIdx.x % P::NB;
   const int tid = threadIdx.x;
-  if (stat_status(W.stats[s]) != SWIFT_WIN_OK) return;
+  if (stat_status(load_stats(R)) != SWIFT_WIN_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* slab = reinterpret_cast<float4*>(smem_raw);  // [N][CB]: (a, b) after pass A
   float2* slab2 = reinterpret_cast<float2*>(smem_raw);  // [N][CB]: G after pass B' (reuses slab)
@@ -698,7 +733,7 @@ __global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch 
   float2* twT = reinterpret_cast<float2*>(xbuf + N);     // [R1][TW]: W_n^(k1 n2)
   for (int i = tid; i < N; i += T) twT[(i % R1) * TW + i / R1] = L.twiddle[i];
   // pass A: task (j, lc) takes rows y = j + R2 m of columns kx and n - kx
-  const float2* zr = W.zr + s * N * N;
+  const float2* zr = R.zr;
 #pragma unroll
   for (int r = 0; r < P::TA / T; ++r) {
     const int task = tid + r * T;
@@ -709,8 +744,8 @@ __global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch 
     float2 a[R1], b[R1];
 #pragma unroll
     for (int m = 0; m < R1; ++m) {
-      const float2 zk = __ldcs(zr + (j + R2 * m) * N + kx);
-      const float2 zn = __ldcs(zr + (j + R2 * m) * N + kn);
+      const float2 zk = __ldcg(zr + (j + R2 * m) * N + kx);
+      const float2 zn = __ldcg(zr + (j + R2 * m) * N + kn);
       if (packed) {
         a[m] = make_float2(2.f * zk.x, 2.f * zn.x);
         b[m] = make_float2(-2.f * zn.y, 2.f * zk.y);
@@ -821,7 +856,7 @@ __global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch 
   }
   __syncthreads();
   // inverse pass A' -> H[y = n2 + R2 n1][kx]
-  float2* hw = W.h + s * N * (N / 2);
+  float2* hw = R.h;
 #pragma unroll
   for (int r = 0; r < P::TA / T; ++r) {
     const int task = tid + r * T;
@@ -834,6 +869,11 @@ __global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch 
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) hw[(n2 + R2 * n1) * (N / 2) + kx] = v[n1];
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch L, const StreamWork W) {
+  cpair_stage<N>(L, slice_ref<N>(L, W, blockIdx.x / PairGeom<N>::NB), blockIdx.x % PairGeom<N>::NB);
 }
 
 // ---------------------------------------------------------------------------
@@ -858,8 +898,8 @@ __device__ __forceinline__ void irow_assemble(const float2* __restrict__ hw, flo
     const int p = e / (N / 2), kx = e % (N / 2);
     if (p < np) {
       const int y1 = y1_of(p), y2 = y1 + N / 2;
-      h1[i] = __ldcs(hw + y1 * (N / 2) + kx);
-      h2[i] = __ldcs(hw + y2 * (N / 2) + kx);
+      h1[i] = __ldcg(hw + y1 * (N / 2) + kx);
+      h2[i] = __ldcg(hw + y2 * (N / 2) + kx);
     }
   }
 #pragma unroll
@@ -918,26 +958,24 @@ __device__ __forceinline__ void irow_passB(const float2* row, const float2* twid
 // WRITE_S: also store the match response s ([n][n] float32 in the Zr space),
 // which the backward pass and the tensor-core schedule read; the plain forward
 // keeps only the block argmax keys and sums.
-template <int N, bool WRITE_S = true>
-__global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, const StreamWork W) {
+template <int N, bool WRITE_S>
+__device__ __forceinline__ void irows_stage(const MatchLaunch& L, const WinRef& R, int pb) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, PB = G::PB, RS = G::RS, T = G::T;
-  const long long s = blockIdx.x / G::NB3;
-  const int pb = blockIdx.x % G::NB3;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (stat_status(W.stats[s]) != SWIFT_WIN_OK) return;
+  if (stat_status(load_stats(R)) != SWIFT_WIN_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [PB][RS]
   float2* twid = slab + PB * RS;
   __shared__ unsigned long long wkey[T / 32];
   __shared__ double wsum[T / 32][2];
   for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
-  const float2* hw = W.h + s * N * (N / 2);
+  const float2* hw = R.h;
   irow_assemble<N, PB, T>(hw, slab, PB, [&](int p) { return pb * PB + p; }, tid);
   __syncthreads();
   irow_passA<N, PB, T>(slab, PB, tid);
   __syncthreads();
-  float* surf = reinterpret_cast<float*>(W.zr + s * N * N);  // [N][N] response
+  float* surf = reinterpret_cast<float*>(R.zr);  // [N][N] response
   // running maxima of the y1 rows and of the y2 rows: each thread meets either
   // set in increasing row-major index, so a strict '>' keeps the smallest
   // index among equal values; one argmax key per set at the end
@@ -991,12 +1029,17 @@ __global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, 
     const double t1 = warp_sum_f64(lane < T / 32 ? wsum[lane][0] : 0.0);
     const double t2 = warp_sum_f64(lane < T / 32 ? wsum[lane][1] : 0.0);
     if (lane == 0) {
-      unsigned long long* part = W.part + 3 * (s * G::NB3 + pb);
+      unsigned long long* part = R.part + 3 * pb;
       part[0] = k;
       part[1] = static_cast<unsigned long long>(__double_as_longlong(t1));
       part[2] = static_cast<unsigned long long>(__double_as_longlong(t2));
     }
   }
+}
+
+template <int N, bool WRITE_S = true>
+__global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, const StreamWork W) {
+  irows_stage<N, WRITE_S>(L, slice_ref<N>(L, W, blockIdx.x / StreamGeom<N>::NB3), blockIdx.x % StreamGeom<N>::NB3);
 }
 
 // Result record from the peak (py, px, value pk), the background sums ta, tc
@@ -1102,22 +1145,16 @@ __global__ void __launch_bounds__(256) stream_final_kernel(const MatchLaunch L, 
 // steps (the values equal K3's bit for bit, so total minus disc is exact up to
 // the FP64 sums) -- a pruned inverse: about 2R + 1 of the n/2 row pairs
 // instead of a full n x n response written and read back.
-template <int N>
-struct PeakGeom {
-  static constexpr int T = 128;  // threads per window
-  static constexpr int PB = 8;   // row pairs per chunk
-};
-
-template <int N>
-__global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L, const StreamWork W) {
+// T threads per window, PB row pairs per chunk (T / 16)
+template <int N, int T>
+__device__ __forceinline__ void peak_stage(const MatchLaunch& L, const WinRef& R) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, RS = G::RS;
-  constexpr int PB = PeakGeom<N>::PB, T = PeakGeom<N>::T;
+  constexpr int PB = T / 16;
   constexpr int TB = PB * R1;
-  const long long s = blockIdx.x;
-  const long long b = W.b0 + s;
+  const long long b = R.b;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int st = stat_status(W.stats[s]);
+  const int st = stat_status(load_stats(R));
   if (st == kStatusSkip) return;
   swift_result* out = L.out + b;
   if (st != SWIFT_WIN_OK) {
@@ -1140,11 +1177,11 @@ __global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L
     unsigned long long gk = 0ull;
     double ta = 0.0, tc = 0.0;
     for (int k = lane; k < G::NB3; k += 32) {
-      const unsigned long long* part = W.part + 3 * (s * G::NB3 + k);
-      const unsigned long long v = part[0];
+      const unsigned long long* part = R.part + 3 * k;
+      const unsigned long long v = __ldcg(part);
       gk = v > gk ? v : gk;
-      ta += __longlong_as_double(static_cast<long long>(part[1]));
-      tc += __longlong_as_double(static_cast<long long>(part[2]));
+      ta += __longlong_as_double(static_cast<long long>(__ldcg(part + 1)));
+      tc += __longlong_as_double(static_cast<long long>(__ldcg(part + 2)));
     }
     gk = warp_max_u64(gk);
     ta = warp_sum_f64(ta);
@@ -1159,16 +1196,16 @@ __global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L
   const unsigned long long gk = s_key;
   const uint32_t pidx = key_index(gk);
   const int py = static_cast<int>(pidx / N), px = static_cast<int>(pidx % N);
-  // rows within R of the peak: the disc (dy^2 + dx^2 <= r2, so |dy| <=
+  // rows within rr of the peak: the disc (dy^2 + dx^2 <= r2, so |dy| <=
   // floor(sqrt(r2))) and the parabola's neighbours (|dy| <= 1)
-  int R = static_cast<int>(sqrtf(L.radius2));
-  while ((R + 1) * (R + 1) <= static_cast<int>(L.radius2)) ++R;
-  while (R * R > static_cast<int>(L.radius2)) --R;
-  R = R < 1 ? 1 : R;
-  // row pairs (y, y + n/2) holding the rows py - R .. py + R: consecutive pair indices
-  const int npairs = 2 * R + 1 < N / 2 ? 2 * R + 1 : N / 2;
-  const int p0 = (py - R) & (N / 2 - 1);
-  const float2* hw = W.h + s * N * (N / 2);
+  int rr = static_cast<int>(sqrtf(L.radius2));
+  while ((rr + 1) * (rr + 1) <= static_cast<int>(L.radius2)) ++rr;
+  while (rr * rr > static_cast<int>(L.radius2)) --rr;
+  rr = rr < 1 ? 1 : rr;
+  // row pairs (y, y + n/2) holding the rows py - rr .. py + rr: consecutive pair indices
+  const int npairs = 2 * rr + 1 < N / 2 ? 2 * rr + 1 : N / 2;
+  const int p0 = (py - rr) & (N / 2 - 1);
+  const float2* hw = R.h;
   double da = 0.0, dc = 0.0, dn = 0.0;
   for (int c0 = 0; c0 < npairs; c0 += PB) {
     const int np = npairs - c0 < PB ? npairs - c0 : PB;
@@ -1198,9 +1235,9 @@ __global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L
     __syncthreads();
     // disc pixels of this chunk's rows (FP64 sums) and the peak's neighbours
     if (warp == 0) {
-      const int D = 2 * R + 1;
+      const int D = 2 * rr + 1;
       for (int e = lane; e < D * D; e += 32) {
-        const int dy = e / D - R, dx = e % D - R;
+        const int dy = e / D - rr, dx = e % D - rr;
         const int y = (py + dy) & (N - 1), x = (px + dx) & (N - 1);
         const int slot = ((y & (N / 2 - 1)) - p0 - c0) & (N / 2 - 1);
         if (slot >= np) continue;  // a row of another chunk
@@ -1236,6 +1273,17 @@ __global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L
     *out = window_result(N, py, px, key_value(gk), s_tot[0] - da, s_tot[1] - dc, static_cast<double>(N) * N - dn,
                          s_nb);
   }
+}
+
+template <int N>
+struct PeakGeom {
+  static constexpr int T = 128;  // threads per window (standalone kernel)
+  static constexpr int PB = T / 16;
+};
+
+template <int N>
+__global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L, const StreamWork W) {
+  peak_stage<N, PeakGeom<N>::T>(L, slice_ref<N>(L, W, blockIdx.x));
 }
 
 // ---------------------------------------------------------------------------

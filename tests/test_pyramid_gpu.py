@@ -193,3 +193,40 @@ def test_stale_ok_status_of_another_level_is_skipped_by_the_row_guard():
     plan.set_test_stale_status(False)
     torch.cuda.synchronize()
     assert torch.equal(stale, base)
+
+
+@pytest.mark.parametrize("sched", ["fused", "stream", "persistent"])
+def test_level_offsets_give_the_level_array_results(pyramid, sched):
+    """A batch sorted by level with its level offsets: each level's launches
+    cover only its own windows; the results equal the level-array call's,
+    bit for bit, in every schedule (the persistent one indexes the ranges
+    itself)."""
+    P = pyramid
+    order = np.argsort(P["lvl"], kind="stable")
+    org, lvl = P["org"][order], P["lvl"][order]
+    offs = [0] + [int((lvl <= k).sum()) for k in range(3)]
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)  # noqa: E731
+    plan = swift.Plan(LEVELS, dtype="u8", max_windows=len(org))
+    for l in range(3):
+        plan.set_schedule(l, sched if (sched != "fused" or LEVELS[l].n <= 256) else "stream")
+    want = plan.match(P["ta"], P["tb"], T(org), T(org), level=T(lvl)).clone()
+    got = plan.match(P["ta"], P["tb"], T(org), T(org), level_offsets=offs)
+    got2 = plan.match(P["ta"], P["tb"], T(org), T(org), level=T(lvl), level_offsets=offs)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want) and torch.equal(got2, want)
+
+
+def test_bad_level_offsets_are_rejected(pyramid):
+    P = pyramid
+    plan = swift.Plan(LEVELS, dtype="u8", max_windows=len(P["org"]))
+    B = len(P["org"])
+    for offs in ([0, 10, 5, B], [1, 10, 20, B], [0, 10, 20, B - 1]):
+        with pytest.raises(ValueError):
+            plan.match(P["ta"], P["tb"], P["to"], P["to"], level_offsets=offs)
+    # the C boundary checks them too
+    import ctypes as C
+    bt, keep, _, _ = plan._batch(P["ta"], P["tb"], P["to"], P["to"], None, None, [0, 10, 20, B])
+    bad = (C.c_int64 * 4)(0, 10, 5, B)
+    bt.level_offsets = bad
+    out = torch.empty((B, 8), dtype=torch.int32, device=DEV)
+    assert swift.lib.swift_match_batch(plan.handle, C.byref(bt), out.data_ptr(), None) == swift._lib.SWIFT_ERR_INVALID_ARG
