@@ -48,6 +48,7 @@ struct swift_plan_s {
   // streaming forward path: its workspace
   void* work = nullptr;
   long long work_windows = 0;  // capacity (windows of the largest streamed size)
+  unsigned int* done = nullptr;  // [work_windows] per-window block counters of the streaming finalize (kept zero)
   // affine-warp forward and backward: allocated on first use
   void* bwork = nullptr;
   long long bwork_windows = 0;
@@ -109,6 +110,7 @@ static swift_status release(swift_plan p) {
     if (p->tc_tab[i]) cudaFree(p->tc_tab[i]);
   }
   if (p->work) cudaFree(p->work);
+  if (p->done) cudaFree(p->done);
   if (p->bwork) cudaFree(p->bwork);
   if (p->pwork) cudaFree(p->pwork);
   if (p->tev) {
@@ -210,7 +212,9 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
   }
   if (per > 0) {
     p->work_windows = max_windows < kStreamSlice ? max_windows : kStreamSlice;
-    if (cudaMalloc(&p->work, per * p->work_windows + 4096) != cudaSuccess) {
+    if (cudaMalloc(&p->work, per * p->work_windows + 4096) != cudaSuccess ||
+        cudaMalloc(&p->done, sizeof(unsigned int) * p->work_windows) != cudaSuccess ||
+        cudaMemset(p->done, 0, sizeof(unsigned int) * p->work_windows) != cudaSuccess) {
       release(p);
       cudaGetLastError();
       return SWIFT_ERR_OOM;
@@ -333,6 +337,7 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
     for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
       const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
       swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
+      W.done = plan->done;
       if (plan->timing) {
         const int set = plan->tcount++ % kTimingSets;
         plan->tkind[set] = 0;

@@ -87,6 +87,8 @@ struct StreamWork {
   long long b0;              // first window of the slice
   long long count;           // windows in the slice
   cudaEvent_t* ev = nullptr; // host: 6 events recorded around the five kernels (timing), or null
+  unsigned int* done = nullptr;  // [S] finished inverse-row blocks per window (zero between calls), or
+                                 // null: the finalize then runs as a kernel of its own
 };
 
 // streaming forward path (swim_stream.cu): bytes of workspace per window, launch of one slice

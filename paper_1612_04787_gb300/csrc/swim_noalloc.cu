@@ -22,6 +22,8 @@ namespace {
 // Static scratch shared by every call on a device (held until the process exits).
 constexpr size_t kNoAllocBytes = 24u << 20;  // 24 MiB
 constexpr size_t kTableBytes = 8192;         // taper (n floats, at 0) + twiddles (n complex, at 2048)
+constexpr size_t kDoneBytes = 2048;          // per-window finalize counters (512), after the tables; they
+                                             // start at zero (static storage) and every call leaves them zero
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of the array, looked up once per device with that device
@@ -44,7 +46,7 @@ cudaError_t scratch_address(int device, void** out) {
 
 long long capacity_for(int n) {
   const size_t per = swift::stream_bytes_per_window(n);
-  return static_cast<long long>((kNoAllocBytes - kTableBytes - 4 * 256) / per);
+  return static_cast<long long>((kNoAllocBytes - kTableBytes - kDoneBytes - 4 * 256) / per);
 }
 
 // taper (n floats) and twiddle table (n complex, [m][j] with j < r1) of a level,
@@ -129,7 +131,8 @@ extern "C" swift_status swift_match_batch_noalloc(const swift_level* level, swif
   L.taper = reinterpret_cast<const float*>(base);
   L.twiddle = reinterpret_cast<const float2*>(base + 2048);
   L.out = out;
-  const swift::StreamWork W = swift::stream_carve(base + kTableBytes, capacity_for(n), n, 0, B);
+  swift::StreamWork W = swift::stream_carve(base + kTableBytes + kDoneBytes, capacity_for(n), n, 0, B);
+  W.done = reinterpret_cast<unsigned int*>(base + kTableBytes);
   if (swift::launch_stream(n, in, L, W, st) != cudaSuccess) return SWIFT_ERR_CUDA;
   return SWIFT_OK;
 }

@@ -191,7 +191,19 @@ __device__ __noinline__ void persist_s3(const MatchLaunch* L, WinRef R, int sub)
 }
 template <int N>
 __device__ __noinline__ void persist_s4(const MatchLaunch* L, WinRef R) {
-  peak_stage<N, 256>(*L, R);
+  // the same finalize as the streaming schedule's (folded into its last
+  // inverse-row block below an 8 px radius, a kernel of its own above)
+  if (L->radius2 < 64.f) {
+    const int st = stat_status(load_stats(R));
+    if (st == SWIFT_WIN_OK) {
+      disc_stage<N>(*L, R);
+    } else if (st != kStatusSkip && threadIdx.x == 0) {
+      swift_result r = {0, 0, 0.f, 0.f, 0.f, 0.f, st, 0};
+      L->out[R.b] = r;
+    }
+  } else {
+    peak_stage<N, 256>(*L, R);
+  }
 }
 
 template <int N, typename TIn>
@@ -207,6 +219,7 @@ __device__ __forceinline__ void persist_stage(const PersistLaunch& P, const Matc
   R.h = P.h + slot * P.nmax * (P.nmax / 2);
   R.part = P.part + kPersistPartStride * R.b;
   R.pre = nullptr;
+  R.done = nullptr;  // the finalize is an item of its own
   if (!live) {
     // the launch aborted: no work; a finalize item reports the window
     if (stage == 4 && threadIdx.x == 0) {

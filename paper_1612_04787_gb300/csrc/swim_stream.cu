@@ -60,9 +60,16 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
     stream_cols_kernel<N><<<S * G::NB2, G::T2, cols_smem<N>(), st>>>(L, W);
   }
   mark(3);
-  stream_irows_kernel<N, false><<<S * G::NB3, 256, irows_smem<N>(), st>>>(L, W);
+  {
+    StreamWork W3 = W;
+    if (!(N <= 256 && L.radius2 < 64.f)) W3.done = nullptr;
+    stream_irows_kernel<N, false><<<S * G::NB3, 256, irows_smem<N>(), st>>>(L, W3);
+  }
   mark(4);
-  stream_peak_kernel<N><<<S, PeakGeom<N>::T, peak_smem<N>(), st>>>(L, W);
+  // n <= 256, exclusion radius below 8 px, block counters given: the last
+  // inverse-row block of each window finalizes it; otherwise a kernel of its own
+  const bool fold = N <= 256 && W.done != nullptr && L.radius2 < 64.f;
+  if (!fold) stream_peak_kernel<N><<<S, PeakGeom<N>::T, peak_smem<N>(), st>>>(L, W);
   mark(5);
   return cudaGetLastError();
 }

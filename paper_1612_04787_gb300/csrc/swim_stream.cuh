@@ -72,12 +72,13 @@ __device__ __forceinline__ int stat_status(const float4& s) { return __float_as_
 // L2 (ld.global.cg): in the persistent schedule another SM may have written
 // them since this SM's L1 last saw those lines.
 struct WinRef {
-  long long b;               // window index in the batch
-  float4* stats;             // [1]
-  float2* zr;                // [n][n]
-  float2* h;                 // [n][n/2]
-  unsigned long long* part;  // [NB3][3]
-  const int* pre;            // status decided before the statistics, or null
+  long long b = 0;                     // window index in the batch
+  float4* stats = nullptr;             // [1]
+  float2* zr = nullptr;                // [n][n]
+  float2* h = nullptr;                 // [n][n/2]
+  unsigned long long* part = nullptr;  // [NB3][3]
+  const int* pre = nullptr;            // status decided before the statistics, or null
+  unsigned int* done = nullptr;        // finished inverse-row blocks of the window (finalize in K3), or null
 };
 
 template <int N>
@@ -89,6 +90,7 @@ __device__ __forceinline__ WinRef slice_ref(const MatchLaunch& L, const StreamWo
   R.h = W.h + s * N * (N / 2);
   R.part = W.part + 3 * s * StreamGeom<N>::NB3;
   R.pre = L.pre_status != nullptr ? L.pre_status + s : nullptr;
+  R.done = W.done != nullptr ? W.done + s : nullptr;
   return R;
 }
 
@@ -958,12 +960,30 @@ __device__ __forceinline__ void irow_passB(const float2* row, const float2* twid
 // WRITE_S: also store the match response s ([n][n] float32 in the Zr space),
 // which the backward pass and the tensor-core schedule read; the plain forward
 // keeps only the block argmax keys and sums.
+template <int N>
+__device__ __forceinline__ void disc_stage(const MatchLaunch& L, const WinRef& R);
+
+// With R.done (n <= 256, exclusion radius below 8 px, plain forward), the
+// block that finishes a window's inverse rows last also finalizes it (peak,
+// SNR, subpixel: disc_stage), so the finalize costs no launch and its latency
+// hides behind other windows' blocks; the block pb = 0 writes the record of a
+// window whose status is not OK.
 template <int N, bool WRITE_S>
 __device__ __forceinline__ void irows_stage(const MatchLaunch& L, const WinRef& R, int pb) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, PB = G::PB, RS = G::RS, T = G::T;
+  constexpr bool kFold = !WRITE_S && N <= 256;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (stat_status(load_stats(R)) != SWIFT_WIN_OK) return;
+  {
+    const int st = stat_status(load_stats(R));
+    if (st != SWIFT_WIN_OK) {
+      if (kFold && R.done != nullptr && pb == 0 && tid == 0 && st != kStatusSkip) {
+        swift_result r = {0, 0, 0.f, 0.f, 0.f, 0.f, st, 0};
+        L.out[R.b] = r;
+      }
+      return;
+    }
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [PB][RS]
   float2* twid = slab + PB * RS;
@@ -1035,10 +1055,27 @@ __device__ __forceinline__ void irows_stage(const MatchLaunch& L, const WinRef& 
       part[2] = static_cast<unsigned long long>(__double_as_longlong(t2));
     }
   }
+  if constexpr (kFold) {
+    if (R.done != nullptr) {
+      __shared__ int s_last;
+      __syncthreads();  // this block's partial is written
+      if (tid == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(R.done, 1u);
+        s_last = prev == static_cast<unsigned int>(G::NB3 - 1);
+        if (s_last) {
+          __threadfence();  // the other blocks' partials are visible to this block
+          *R.done = 0u;     // ready for the next call
+        }
+      }
+      __syncthreads();
+      if (s_last) disc_stage<N>(L, R);
+    }
+  }
 }
 
 template <int N, bool WRITE_S = true>
-__global__ void __launch_bounds__(256) stream_irows_kernel(const MatchLaunch L, const StreamWork W) {
+__global__ void __launch_bounds__(256, 5) stream_irows_kernel(const MatchLaunch L, const StreamWork W) {
   irows_stage<N, WRITE_S>(L, slice_ref<N>(L, W, blockIdx.x / StreamGeom<N>::NB3), blockIdx.x % StreamGeom<N>::NB3);
 }
 
@@ -1078,6 +1115,102 @@ __device__ __forceinline__ swift_result window_result(int n, int py, int px, flo
   r.status = SWIFT_WIN_OK;
   r.reserved = 0;
   return r;
+}
+
+// Finalize of one window by the last of its inverse-row blocks (256
+// threads, exclusion radius below 8 px): the global argmax and totals from
+// the blocks' partials, the rows py - R .. py + R recomputed with the
+// inverse-row steps (the values equal the blocks' own bit for bit), the
+// (2R + 1)^2 values around the peak kept in shared memory, the disc sums in
+// FP64 and the record.
+template <int N>
+__device__ __forceinline__ void disc_stage(const MatchLaunch& L, const WinRef& R) {
+  using G = StreamGeom<N>;
+  constexpr int R1 = G::R1, R2 = G::R2, RS = G::RS, T = 256, PB = 16;
+  constexpr int TB = PB * R1;
+  constexpr int RMAX = 7;
+  constexpr int DW = 2 * RMAX + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* slab = reinterpret_cast<float2*>(smem_raw);  // [PB][RS]
+  float2* twid = slab + PB * RS;
+  __shared__ unsigned long long d_key;
+  __shared__ double d_tot[2];
+  __shared__ float d_val[DW][DW];  // s around the peak, [dy + R][dx + R]
+  __syncthreads();  // the block's own inverse rows are done with the shared memory
+  for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
+  if (warp == 0) {
+    unsigned long long gk = 0ull;
+    double ta = 0.0, tc = 0.0;
+    for (int k = lane; k < G::NB3; k += 32) {
+      const unsigned long long* part = R.part + 3 * k;
+      const unsigned long long v = __ldcg(part);
+      gk = v > gk ? v : gk;
+      ta += __longlong_as_double(static_cast<long long>(__ldcg(part + 1)));
+      tc += __longlong_as_double(static_cast<long long>(__ldcg(part + 2)));
+    }
+    gk = warp_max_u64(gk);
+    ta = warp_sum_f64(ta);
+    tc = warp_sum_f64(tc);
+    if (lane == 0) {
+      d_key = gk;
+      d_tot[0] = ta;
+      d_tot[1] = tc;
+    }
+  }
+  __syncthreads();
+  const unsigned long long gk = d_key;
+  const uint32_t pidx = key_index(gk);
+  const int py = static_cast<int>(pidx / N), px = static_cast<int>(pidx % N);
+  int rr = static_cast<int>(sqrtf(L.radius2));
+  while ((rr + 1) * (rr + 1) <= static_cast<int>(L.radius2)) ++rr;
+  while (rr * rr > static_cast<int>(L.radius2)) --rr;
+  rr = rr < 1 ? 1 : rr;  // at most RMAX: the host folds the finalize only for r2 < 64
+  const int np = 2 * rr + 1;  // row pairs holding the rows py - rr .. py + rr
+  const int p0 = (py - rr) & (N / 2 - 1);
+  irow_assemble<N, PB, T>(R.h, slab, np, [&](int p) { return (p0 + p) & (N / 2 - 1); }, tid);
+  __syncthreads();
+  irow_passA<N, PB, T>(slab, np, tid);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < (TB + T - 1) / T; ++i) {
+    const int task = tid + i * T;
+    if ((TB % T != 0 && task >= TB) || task / R1 >= np) continue;
+    const int p = task / R1, k1 = task % R1;
+    float2 v[R2];
+    irow_passB<N>(slab + p * RS, twid, k1, v);
+    const int y1 = (p0 + p) & (N / 2 - 1);
+    const int dy1 = ((y1 - py + N / 2) & (N - 1)) - N / 2, dy2 = ((y1 + N / 2 - py + N / 2) & (N - 1)) - N / 2;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int dx = ((k1 + R1 * k2 - px + N / 2) & (N - 1)) - N / 2;
+      if (dx >= -rr && dx <= rr) {
+        if (dy1 >= -rr && dy1 <= rr) d_val[dy1 + RMAX][dx + RMAX] = v[k2].x;
+        if (dy2 >= -rr && dy2 <= rr) d_val[dy2 + RMAX][dx + RMAX] = v[k2].y;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double da = 0.0, dc = 0.0, dn = 0.0;
+    for (int e = lane; e < np * np; e += 32) {
+      const int dy = e / np - rr, dx = e % np - rr;
+      if (dy * dy + dx * dx <= static_cast<int>(L.radius2)) {
+        const double d = d_val[dy + RMAX][dx + RMAX];
+        da += d;
+        dc += d * d;
+        dn += 1.0;
+      }
+    }
+    da = warp_sum_f64(da);
+    dc = warp_sum_f64(dc);
+    dn = warp_sum_f64(dn);
+    if (lane == 0) {
+      const float nb[4] = {d_val[RMAX - 1][RMAX], d_val[RMAX + 1][RMAX], d_val[RMAX][RMAX - 1], d_val[RMAX][RMAX + 1]};
+      L.out[R.b] = window_result(N, py, px, key_value(gk), d_tot[0] - da, d_tot[1] - dc,
+                                 static_cast<double>(N) * N - dn, nb);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

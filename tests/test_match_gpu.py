@@ -329,3 +329,18 @@ def test_512_schedule_and_warp_limits():
     with pytest.raises(swift.SwiftError) as e:
         plan.match(sec, sec, org, org, affine=torch.zeros((2, 6), dtype=torch.float32, device=DEV))
     assert "UNSUPPORTED" in str(e.value)
+
+
+@pytest.mark.parametrize("n", [128, 256])
+@pytest.mark.parametrize("radius", [0.0, 0.9, 1.0, 7.9, 8.0, 20.0])
+def test_exclusion_radius_range(sections, n, radius):
+    """The finalize in its two forms: folded into the last inverse-row block
+    (radius below 8 px: the rows within the radius recomputed) and as a kernel
+    of its own (8 px and more, several chunks of row pairs at 20 px), and the
+    smallest radii (the parabola's neighbours still recomputed)."""
+    a, b = sections
+    ro = synth.random_origins(10, 1024, 1024, n, seed=int(10 * radius) + n)
+    mo = np.clip(ro + np.random.default_rng(n).integers(-6, 7, ro.shape), 0, 1024 - n).astype(np.int32)
+    lv = swift.Level(n, 0.65, "hann", 1.0, radius)
+    g = run_sections(a, b, ro, mo, lv)
+    check_sections(a, b, ro, mo, lv, g, f"n={n} r={radius}")
