@@ -264,6 +264,26 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Warp sum of FP32 values carried as an unevaluated float pair (hi + lo, the
+// error of every addition kept by Knuth's TwoSum), returned as a double: about
+// 48 significant bits from FP32 additions only.  This GPU's FP64 unit issues
+// a warp instruction every few dozen cycles, so an FP64 butterfly makes the
+// per-warp block sums of the streaming kernels wait on it.  Every lane ends
+// with the same pair: TwoSum's (s, e) is exact and symmetric in its operands.
+__device__ __forceinline__ double warp_sum_ff(float v) {
+  float hi = v, lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ohi = __shfl_xor_sync(0xffffffffu, hi, o), olo = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, ohi);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(ohi, bb));
+    const float t = __fadd_rn(e, __fadd_rn(lo, olo));
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+  }
+  return static_cast<double>(hi) + static_cast<double>(lo);
+}
 __device__ __forceinline__ float warp_sum_f32(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -210,7 +210,7 @@ __device__ __forceinline__ void stats_stage(const MatchLaunch& L, const WinRef& 
       accum(tap[y] * tap[x], mv, rv);
     }
   }
-  double dm = warp_sum_f64(static_cast<double>(sm)), dr = warp_sum_f64(static_cast<double>(sr));
+  const double dm = warp_sum_ff(sm), dr = warp_sum_ff(sr);
   float a0 = warp_min_f32(mn_m), a1 = warp_max_f32(mx_m), a2 = warp_min_f32(mn_r), a3 = warp_max_f32(mx_r);
   int bb = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
@@ -1037,7 +1037,7 @@ __device__ __forceinline__ void irows_stage(const MatchLaunch& L, const WinRef& 
     best = ka > kb ? ka : kb;
   }
   best = warp_max_u64(best);
-  const double d1 = warp_sum_f64(static_cast<double>(s1)), d2 = warp_sum_f64(static_cast<double>(s2));
+  const double d1 = warp_sum_ff(s1), d2 = warp_sum_ff(s2);
   if (lane == 0) {
     wkey[warp] = best;
     wsum[warp][0] = d1;
