@@ -270,8 +270,7 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 // a warp instruction every few dozen cycles, so an FP64 butterfly makes the
 // per-warp block sums of the streaming kernels wait on it.  Every lane ends
 // with the same pair: TwoSum's (s, e) is exact and symmetric in its operands.
-__device__ __forceinline__ double warp_sum_ff(float v) {
-  float hi = v, lo = 0.f;
+__device__ __forceinline__ void warp_sum_ff2(float& hi, float& lo) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float ohi = __shfl_xor_sync(0xffffffffu, hi, o), olo = __shfl_xor_sync(0xffffffffu, lo, o);
@@ -282,6 +281,10 @@ __device__ __forceinline__ double warp_sum_ff(float v) {
     hi = __fadd_rn(s, t);
     lo = __fsub_rn(t, __fsub_rn(hi, s));
   }
+}
+__device__ __forceinline__ double warp_sum_ff(float v) {
+  float hi = v, lo = 0.f;
+  warp_sum_ff2(hi, lo);
   return static_cast<double>(hi) + static_cast<double>(lo);
 }
 __device__ __forceinline__ float warp_sum_f32(float v) {
@@ -301,6 +304,66 @@ __device__ __forceinline__ float warp_max_f32(float v) {
 }
 
 // ---------------------------------------------------------------------------
+// the record of one window (Sec. III): the peak, its SNR against the
+// background outside the exclusion disc, the parabola subpixel fit
+// ---------------------------------------------------------------------------
+// Peak (py, px, value pk); ta, tc, tn: the sum of s, the sum of s^2 and the
+// number of background pixels (FP64 sums); nb: the wrapped neighbours
+// s(py-1, px), s(py+1, px), s(py, px-1), s(py, px+1).  SNR = (pk - mu) / sigma
+// (population sigma; +inf when sigma = 0 and the peak is above the mean), a
+// separable 3-point parabola per axis clamped to [-1/2, 1/2] (0 when not
+// concave), shifts in [-n/2, n/2).  The background mean and
+// variance are formed in FP64; the ratios that follow need no FP64 (their
+// results are stored as FP32): this GPU's FP64 divide and square root are
+// long chains on a slow unit, on the critical path of every window.
+//   1 / tn: the FP32 reciprocal (correctly rounded; tn is an integer below
+//     2^24) refined by one Newton-Raphson step x + x (1 - tn x), about 46 bits;
+//   SNR = (peak - mean) / sqrt(var): FP32 reciprocal square root of the FP64
+//     variance (a variance below the FP32 normal range takes the FP64 route);
+//   parabola: numerator and denominator exact in FP64 (sums of three FP32
+//     values), their ratio in FP32.
+__device__ __forceinline__ swift_result window_result(int n, int py, int px, float pkf, double ta, double tc,
+                                                      double tn, const float* nb) {
+  const double x0 = static_cast<double>(__frcp_rn(static_cast<float>(tn)));
+  const double inv = fma(x0, fma(-tn, x0, 1.0), x0);
+  const double mu = ta * inv;
+  const double var = fma(tc, inv, -mu * mu);
+  const double pk = static_cast<double>(pkf);
+  float snr;
+  if (var > 0.0) {
+    const float vf = static_cast<float>(var);
+    if (vf >= 1.17549435e-38f) {
+      snr = static_cast<float>(pk - mu) * rsqrtf(vf);
+    } else {
+      snr = static_cast<float>((pk - mu) / sqrt(var));
+    }
+  } else {
+    snr = pk > mu ? __int_as_float(0x7f800000) : 0.f;
+  }
+  auto parab = [](float sm, float s0, float sp) -> float {
+    const double den = static_cast<double>(sm) - 2.0 * static_cast<double>(s0) + static_cast<double>(sp);
+    if (!(den < 0.0)) return 0.f;
+    const float d = 0.5f * static_cast<float>(static_cast<double>(sm) - static_cast<double>(sp)) /
+                    static_cast<float>(den);
+    return d < -0.5f ? -0.5f : (d > 0.5f ? 0.5f : d);
+  };
+  const float fy = parab(nb[0], pkf, nb[1]);
+  const float fx = parab(nb[2], pkf, nb[3]);
+  const int dy = py < n / 2 ? py : py - n;
+  const int dx = px < n / 2 ? px : px - n;
+  swift_result r;
+  r.dy = dy;
+  r.dx = dx;
+  r.sy = static_cast<float>(dy) + fy;
+  r.sx = static_cast<float>(dx) + fx;
+  r.snr = snr;
+  r.peak = pkf;
+  r.status = SWIFT_WIN_OK;
+  r.reserved = 0;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
 // shared-memory scratch besides the slab
 // ---------------------------------------------------------------------------
 constexpr int kMaxC = 8;
@@ -312,11 +375,12 @@ struct WinInfo {
 struct __align__(16) Scratch {
   WinInfo win[2];
   unsigned long long mbar;  // staged-load barrier
-  double wsum[32][2];
+  float wsum[32][2];
   float wmin[32][2], wmax[32][2];
   int wbad[32];
   unsigned long long wkey[32];
-  double wbg[32][3];
+  float wbg[32][4];  // per warp: sum s (hi, lo), sum s^2 (hi, lo)
+  int wcnt[32];
   // cluster all-gather slots: written by every CTA into every CTA
   double csum[kMaxC][2];
   float cmin[kMaxC][2], cmax[kMaxC][2];
@@ -383,14 +447,6 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
     twid[i] = L.twiddle[i];
     taper[i] = L.taper[i];
   }
-  if (tid == 0) {
-    sc->broken = 0;
-    if constexpr (BULK) {
-      mbar_init(mbar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-  }
-  __syncthreads();
 
   // Window descriptors live in shared memory, double-buffered: lane 0 of
   // warp 0 finds the next window of this cluster's stride set (skipping other
@@ -434,7 +490,65 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
     }
   };
 
-  if (tid == 0) fetch_info(0, cid);
+  const float inv_k = 1.0f / static_cast<float>(L.ref_count);
+  // raw pixels of one window straight from global memory into the thread's
+  // pass-A registers (no staging)
+  float mraw[P::KA][R1], rraw[P::KA][R1];
+  auto load_direct = [&](const WinInfo& wi) {
+    const TIn* mbase;
+    const TIn* rbase;
+    long long mpitch, rpitch;
+    if (L.patch_mode) {
+      mbase = static_cast<const TIn*>(L.mov) + wi.w * L.mov_stride;
+      rbase = static_cast<const TIn*>(L.ref) + wi.w * L.ref_stride;
+      mpitch = rpitch = N;
+    } else {
+      mbase = static_cast<const TIn*>(L.mov) + static_cast<long long>(wi.my) * L.mov_pitch + wi.mx;
+      rbase = static_cast<const TIn*>(L.ref) + static_cast<long long>(wi.ry) * L.ref_pitch + wi.rx;
+      mpitch = L.mov_pitch;
+      rpitch = L.ref_pitch;
+    }
+#pragma unroll
+    for (int i = 0; i < P::KA; ++i) {
+      const int task = tid + i * T;
+      const int line = task / R2, j = task % R2;
+      const int y = rank * ROWS + line;
+      const TIn* mrow = mbase + y * mpitch + j;
+      const TIn* rrow = rbase + y * rpitch + j;
+#pragma unroll
+      for (int m = 0; m < R1; ++m) {
+        mraw[i][m] = load_px<TIn>(mrow + R2 * m);
+        float rv = load_px<TIn>(rrow + R2 * m);
+        for (int k = 1; k < L.ref_count; ++k) rv += load_px<TIn>(rrow + k * L.ref_stride + R2 * m);
+        rraw[i][m] = L.ref_count > 1 ? rv * inv_k : rv;
+      }
+    }
+  };
+  // patch stacks of one level (64 x 64: the single-window latency case; the
+  // larger kernels would keep their pixel registers live across windows): the
+  // first window needs no descriptor, so its pixels are requested together
+  // with the tables (one memory latency instead of two before the first
+  // transform)
+  bool preloaded = false;
+  if constexpr (!BULK && N == 64) {
+    if (L.patch_mode && L.level_idx == nullptr && cid < B) {
+      WinInfo w0;
+      w0.w = cid;
+      w0.my = w0.mx = w0.ry = w0.rx = 0;
+      w0.ok = 1;
+      load_direct(w0);
+      preloaded = true;
+    }
+  }
+  // the first descriptor's loads overlap the table loads above
+  if (tid == 0) {
+    sc->broken = 0;
+    if constexpr (BULK) {
+      mbar_init(mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fetch_info(0, cid);
+  }
   __syncthreads();
   int cur = 0;
   if (BULK && warp == 0) {
@@ -442,7 +556,6 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
     if (wi.w < B && wi.ok) prefetch(wi);
   }
   uint32_t parity = 0;
-  const float inv_k = 1.0f / static_cast<float>(L.ref_count);
   const float half_w = -0.5f * L.w;
   const float inv_n2 = 1.0f / (static_cast<float>(N) * static_cast<float>(N));
 
@@ -467,7 +580,6 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
 
     // ---- load raw pixels for row pass A; window statistics ----------------
     // task (line, j): elements x = j + R2 m, m < R1, of row rank*ROWS + line
-    float mraw[P::KA][R1], rraw[P::KA][R1];
     float s_m = 0.f, s_r = 0.f;
     float mn_m = 3.4e38f, mx_m = -3.4e38f, mn_r = 3.4e38f, mx_r = -3.4e38f;
     int bad = 0;
@@ -488,34 +600,8 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
         }
       }
     } else {
-      const TIn* mbase;
-      const TIn* rbase;
-      long long mpitch, rpitch;
-      if (L.patch_mode) {
-        mbase = static_cast<const TIn*>(L.mov) + wi.w * L.mov_stride;
-        rbase = static_cast<const TIn*>(L.ref) + wi.w * L.ref_stride;
-        mpitch = rpitch = N;
-      } else {
-        mbase = static_cast<const TIn*>(L.mov) + static_cast<long long>(wi.my) * L.mov_pitch + wi.mx;
-        rbase = static_cast<const TIn*>(L.ref) + static_cast<long long>(wi.ry) * L.ref_pitch + wi.rx;
-        mpitch = L.mov_pitch;
-        rpitch = L.ref_pitch;
-      }
-#pragma unroll
-      for (int i = 0; i < P::KA; ++i) {
-        const int task = tid + i * T;
-        const int line = task / R2, j = task % R2;
-        const int y = rank * ROWS + line;
-        const TIn* mrow = mbase + y * mpitch + j;
-        const TIn* rrow = rbase + y * rpitch + j;
-#pragma unroll
-        for (int m = 0; m < R1; ++m) {
-          mraw[i][m] = load_px<TIn>(mrow + R2 * m);
-          float rv = load_px<TIn>(rrow + R2 * m);
-          for (int k = 1; k < L.ref_count; ++k) rv += load_px<TIn>(rrow + k * L.ref_stride + R2 * m);
-          rraw[i][m] = L.ref_count > 1 ? rv * inv_k : rv;
-        }
-      }
+      if (!preloaded) load_direct(wi);
+      preloaded = false;
     }
 #pragma unroll
     for (int i = 0; i < P::KA; ++i) {
@@ -561,12 +647,11 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
       }
     } else if (warp == 1) {
       // block statistics, all-gathered into every CTA of the cluster
-      double a = lane < NW ? sc->wsum[lane][0] : 0.0, c = lane < NW ? sc->wsum[lane][1] : 0.0;
+      const double a = warp_sum_ff(lane < NW ? sc->wsum[lane][0] : 0.f);
+      const double c = warp_sum_ff(lane < NW ? sc->wsum[lane][1] : 0.f);
       float e = lane < NW ? sc->wmin[lane][0] : 3.4e38f, f = lane < NW ? sc->wmax[lane][0] : -3.4e38f;
       float g = lane < NW ? sc->wmin[lane][1] : 3.4e38f, h = lane < NW ? sc->wmax[lane][1] : -3.4e38f;
       int bb = (lane < NW ? sc->wbad[lane] : 0) | sc->broken;
-      a = warp_sum_f64(a);
-      c = warp_sum_f64(c);
       e = warp_min_f32(e);
       f = warp_max_f32(f);
       g = warp_min_f32(g);
@@ -633,7 +718,12 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
 #pragma unroll
       for (int q = 0; q < R1; ++q) row[P::phys(j + R2 * q)] = v[q];
     }
-    __syncthreads();
+    // with R1 = R2 pass B reads only what the same warp's lanes wrote in pass A
+    if constexpr (R1 == R2) {
+      __syncwarp();
+    } else {
+      __syncthreads();
+    }
 
     // ---- row pass B: block R2 k1 + n2, twiddle, DFT_R2, push to columns ----
     {
@@ -808,7 +898,11 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
 #pragma unroll
       for (int q = 0; q < R1; ++q) row[P::phys(j + R2 * q)] = v[q];
     }
-    __syncthreads();
+    if constexpr (R1 == R2) {  // the same lanes' packed row, as in the forward rows
+      __syncwarp();
+    } else {
+      __syncthreads();
+    }
 
     // ---- inverse row pass B -> surface (kept in place), argmax ---------------
     // the surface stays in place (re: row y1, im: row y2 of each packed line);
@@ -870,7 +964,8 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
 
     // ---- SNR background partials (outside the exclusion disc) ---------------
     {
-      float s1 = 0.f, s2 = 0.f, cnt = 0.f;
+      float s1 = 0.f, s2 = 0.f;
+      int cnt = 0;
 #pragma unroll
       for (int i = 0; i < P::KBh; ++i) {
         const int task = tid + i * T;
@@ -892,30 +987,39 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
             if (static_cast<float>(dya * dya + dx * dx) > L.radius2) {
               s1 += sa;
               s2 = fmaf(sa, sa, s2);
-              cnt += 1.f;
+              ++cnt;
             }
             if (static_cast<float>(dyb * dyb + dx * dx) > L.radius2) {
               s1 += sb;
               s2 = fmaf(sb, sb, s2);
-              cnt += 1.f;
+              ++cnt;
             }
           }
         }
       }
-      double a = warp_sum_f64(static_cast<double>(s1));
-      double c = warp_sum_f64(static_cast<double>(s2));
-      double n = warp_sum_f64(static_cast<double>(cnt));
+      // float-pair warp sums (FP32 instructions only), integer counts
+      float a1 = s1, e1 = 0.f, a2 = s2, e2 = 0.f;
+      warp_sum_ff2(a1, e1);
+      warp_sum_ff2(a2, e2);
+      const int nw = __reduce_add_sync(0xffffffffu, cnt);
       if (lane == 0) {
-        sc->wbg[warp][0] = a;
-        sc->wbg[warp][1] = c;
-        sc->wbg[warp][2] = n;
+        sc->wbg[warp][0] = a1;
+        sc->wbg[warp][1] = e1;
+        sc->wbg[warp][2] = a2;
+        sc->wbg[warp][3] = e2;
+        sc->wcnt[warp] = nw;
       }
     }
     __syncthreads();
     if (warp == 0) {
-      const double a = warp_sum_f64(lane < NW ? sc->wbg[lane][0] : 0.0);
-      const double c = warp_sum_f64(lane < NW ? sc->wbg[lane][1] : 0.0);
-      const double n = warp_sum_f64(lane < NW ? sc->wbg[lane][2] : 0.0);
+      float a1 = lane < NW ? sc->wbg[lane][0] : 0.f, e1 = lane < NW ? sc->wbg[lane][1] : 0.f;
+      float a2 = lane < NW ? sc->wbg[lane][2] : 0.f, e2 = lane < NW ? sc->wbg[lane][3] : 0.f;
+      warp_sum_ff2(a1, e1);
+      warp_sum_ff2(a2, e2);
+      const int nc = __reduce_add_sync(0xffffffffu, lane < NW ? sc->wcnt[lane] : 0);
+      const double a = static_cast<double>(a1) + static_cast<double>(e1);
+      const double c = static_cast<double>(a2) + static_cast<double>(e2);
+      const double n = static_cast<double>(nc);
       if (lane == 0) {
         const uint32_t dst = map_rank<C>(smem_addr(&sc->cbg[rank][0]), 0);
         st_cl_f64<C>(dst, a);
@@ -941,34 +1045,8 @@ __global__ void __launch_bounds__(Plan2D<N, C>::T, Geometry<N, C>::MINB) swim_fo
         c += sc->cbg[r][1];
         n += sc->cbg[r][2];
       }
-      const double mu = a / n;
-      const double var = c / n - mu * mu;
-      const double pk = static_cast<double>(key_value(gk));
-      double snr;
-      if (var > 0.0) {
-        snr = (pk - mu) / sqrt(var);
-      } else {
-        snr = pk > mu ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
-      }
-      auto parab = [](double sm, double s0, double sp) -> double {
-        const double den = sm - 2.0 * s0 + sp;
-        if (!(den < 0.0)) return 0.0;
-        const double d = 0.5 * (sm - sp) / den;
-        return d < -0.5 ? -0.5 : (d > 0.5 ? 0.5 : d);
-      };
-      const double fy = parab(sc->nb[0], pk, sc->nb[1]);
-      const double fx = parab(sc->nb[2], pk, sc->nb[3]);
-      const int dy = py < N / 2 ? py : py - N;
-      const int dx = px < N / 2 ? px : px - N;
-      swift_result r;
-      r.dy = dy;
-      r.dx = dx;
-      r.sy = static_cast<float>(dy + fy);
-      r.sx = static_cast<float>(dx + fx);
-      r.snr = static_cast<float>(snr);
-      r.peak = static_cast<float>(pk);
-      r.status = sc->broken ? SWIFT_WIN_TIMEOUT : SWIFT_WIN_OK;
-      r.reserved = 0;
+      swift_result r = window_result(N, py, px, key_value(gk), a, c, n, sc->nb);
+      if (sc->broken) r.status = SWIFT_WIN_TIMEOUT;
       *out = r;
     }
     cur ^= 1;

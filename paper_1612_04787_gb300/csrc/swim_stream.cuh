@@ -1079,44 +1079,6 @@ __global__ void __launch_bounds__(256, 5) stream_irows_kernel(const MatchLaunch 
   irows_stage<N, WRITE_S>(L, slice_ref<N>(L, W, blockIdx.x / StreamGeom<N>::NB3), blockIdx.x % StreamGeom<N>::NB3);
 }
 
-// Result record from the peak (py, px, value pk), the background sums ta, tc
-// over tn pixels, and the wrapped neighbours nb = s(py-1, px), s(py+1, px),
-// s(py, px-1), s(py, px+1): SNR = (pk - mu) / sigma (population sigma; +inf
-// when sigma = 0 and the peak is above the mean), separable 3-point parabola
-// per axis clamped to [-1/2, 1/2] (0 when not concave), shifts in [-n/2, n/2).
-__device__ __forceinline__ swift_result window_result(int n, int py, int px, float pkf, double ta, double tc,
-                                                      double tn, const float* nb) {
-  const double mu = ta / tn;
-  const double var = tc / tn - mu * mu;
-  const double pk = static_cast<double>(pkf);
-  double snr;
-  if (var > 0.0) {
-    snr = (pk - mu) / sqrt(var);
-  } else {
-    snr = pk > mu ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
-  }
-  auto parab = [](double sm, double s0, double sp) -> double {
-    const double den = sm - 2.0 * s0 + sp;
-    if (!(den < 0.0)) return 0.0;
-    const double d = 0.5 * (sm - sp) / den;
-    return d < -0.5 ? -0.5 : (d > 0.5 ? 0.5 : d);
-  };
-  const double fy = parab(nb[0], pk, nb[1]);
-  const double fx = parab(nb[2], pk, nb[3]);
-  const int dy = py < n / 2 ? py : py - n;
-  const int dx = px < n / 2 ? px : px - n;
-  swift_result r;
-  r.dy = dy;
-  r.dx = dx;
-  r.sy = static_cast<float>(dy + fy);
-  r.sx = static_cast<float>(dx + fx);
-  r.snr = static_cast<float>(snr);
-  r.peak = static_cast<float>(pk);
-  r.status = SWIFT_WIN_OK;
-  r.reserved = 0;
-  return r;
-}
-
 // Finalize of one window by the last of its inverse-row blocks (256
 // threads, exclusion radius below 8 px): the global argmax and totals from
 // the blocks' partials, the rows py - R .. py + R recomputed with the
