@@ -167,6 +167,17 @@ __device__ __forceinline__ void stats_stage(const MatchLaunch& L, const WinRef& 
     float tx[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) tx[k] = tap[x0 + k];
+    // uint8: a window is flat when every pixel equals every other, so each
+    // thread ORs together the XOR of its packed words with its first pixel
+    // replicated (one logic instruction a word) instead of per-pixel minima
+    // and maxima; each vector's tapered sum is a dot product with the column
+    // tapers, scaled by the row taper once: sum_x a_y a_x m = a_y (sum_x a_x m)
+    uint32_t rep_m = 0u, rep_r = 0u, diff_m = 0u, diff_r = 0u;
+    if constexpr (sizeof(TIn) == 1) {
+      const int y0 = tid / (N / VEC);
+      rep_m = 0x01010101u * __ldg(reinterpret_cast<const unsigned char*>(mbase + y0 * mpitch + x0));
+      rep_r = 0x01010101u * __ldg(reinterpret_cast<const unsigned char*>(rbase + y0 * rpitch + x0));
+    }
 #pragma unroll 1
     for (int i0 = 0; i0 < PER; i0 += BATCH) {
       uint4 mqs[BATCH], rqs[BATCH];
@@ -184,11 +195,18 @@ __device__ __forceinline__ void stats_stage(const MatchLaunch& L, const WinRef& 
         if constexpr (sizeof(TIn) == 1) {
           const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w}, rw[4] = {rq.x, rq.y, rq.z, rq.w};
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const float mv = static_cast<float>((mw[k >> 2] >> (8 * (k & 3))) & 0xffu);
-            const float rv = static_cast<float>((rw[k >> 2] >> (8 * (k & 3))) & 0xffu);
-            accum(ay * tx[k], mv, rv);
+          for (int q = 0; q < 4; ++q) {
+            diff_m |= mw[q] ^ rep_m;
+            diff_r |= rw[q] ^ rep_r;
           }
+          float dm = 0.f, dr = 0.f;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            dm = fmaf(tx[k], static_cast<float>((mw[k >> 2] >> (8 * (k & 3))) & 0xffu), dm);
+            dr = fmaf(tx[k], static_cast<float>((rw[k >> 2] >> (8 * (k & 3))) & 0xffu), dr);
+          }
+          sm = fmaf(ay, dm, sm);
+          sr = fmaf(ay, dr, sr);
         } else {
           const float mf[4] = {__uint_as_float(mq.x), __uint_as_float(mq.y), __uint_as_float(mq.z),
                                __uint_as_float(mq.w)};
@@ -198,6 +216,13 @@ __device__ __forceinline__ void stats_stage(const MatchLaunch& L, const WinRef& 
           for (int k = 0; k < 4; ++k) accum(ay * tx[k], mf[k], rf[k]);
         }
       }
+    }
+    if constexpr (sizeof(TIn) == 1) {
+      // as extremes for the block reduction: the thread's first pixel, and a
+      // maximum no byte takes when its pixels differ (flat: global min = max)
+      const float f_m = static_cast<float>(rep_m & 0xffu), f_r = static_cast<float>(rep_r & 0xffu);
+      mn_m = f_m, mx_m = diff_m ? 256.f : f_m;
+      mn_r = f_r, mx_r = diff_r ? 256.f : f_r;
     }
   } else {
     for (int e = tid; e < N * N; e += 256) {  // consecutive threads, consecutive x
