@@ -257,9 +257,12 @@ swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, con
  *               memory of one CTA (64 x 64) or of a cluster of 2 (128 x 128)
  *               or 8 (256 x 256) CTAs, with the row/column redistributions
  *               through distributed shared memory
- *   STREAM      five kernels per level (statistics, rows, column pairs,
- *               inverse rows, finalize) of independent CTAs passing each
- *               window's intermediates through the plan's workspace
+ *   STREAM      four or five kernels per slice of a level's windows
+ *               (statistics, rows, column pairs, inverse rows; a finalize
+ *               kernel only for exclusion radii of 8 px and more, else the
+ *               last inverse-row block of each window finalizes it) of
+ *               independent CTAs passing each window's intermediates through
+ *               the plan's workspace
  *   PERSISTENT  the same five steps as work items of ONE kernel for every
  *               level that has this schedule: CTAs claim items in a fixed
  *               order from a queue and wait (bounded) for the items they
@@ -271,7 +274,14 @@ swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, con
  *               grows to the largest batch matched (a call that must grow it
  *               may not be captured into a graph: swift_plan_capture makes an
  *               uncaptured call first)
- *   DEFAULT     PERSISTENT up to 256 x 256, STREAM for 512 x 512 */
+ *   DEFAULT     FUSED for 64 x 64, STREAM for 128 x 128 and larger
+ * An FP32 forward call spreads its launch units (each fused launch, each
+ * streaming slice) over lanes: the call's stream and one auxiliary stream of
+ * the plan, each lane with its own part of the workspace, so that one unit's
+ * tail overlaps another's head.  The auxiliary lane waits for the work queued
+ * on the call's stream before the call, and the call's stream waits for the
+ * auxiliary lane at its end: the call stays one stream-ordered unit (also
+ * inside a captured graph).  See swift_plan_set_lanes. */
 typedef enum {
   SWIFT_SCHED_DEFAULT = 0,
   SWIFT_SCHED_FUSED = 1,
@@ -288,7 +298,8 @@ swift_status swift_plan_set_schedule(swift_plan plan, int32_t level, int32_t sch
  * level that has it, at each skew of the persistent work order (4, 8, 12,
  * 16 windows between consecutive steps of a window: larger skews leave more
  * items between a producer and its consumer, smaller ones keep a smaller
- * ring in L2), and keeps the fastest for later calls.  `chosen` (host int32
+ * ring in L2), then the chosen schedules with one lane and with two, and
+ * keeps the fastest for later calls.  `chosen` (host int32
  * [n_levels], may be NULL) receives the schedule of each level.  On return
  * `out` holds the batch's results under the chosen schedules. */
 swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swift_result* out, void* stream,
@@ -300,6 +311,16 @@ swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swif
  * keep fewer windows in flight (a smaller ring of workspace slots, 5 * skew +
  * 4, to hold in L2).  The autotuner sets it too. */
 swift_status swift_plan_set_skew(swift_plan plan, int32_t skew);
+
+/* Lanes of the plan's FP32 forward calls (1 or 2; default 2; the autotuner
+ * sets it too).  With 1 every launch goes to the call's stream and a
+ * streaming slice holds up to min(max_windows, 2048) windows; with 2 the
+ * slices hold up to half of that, alternating between the two lanes.  The
+ * results do not depend on the lanes.  SWIFT_ERR_INVALID_ARG for other
+ * values. */
+swift_status swift_plan_set_lanes(swift_plan plan, int32_t lanes);
+/* The plan's current lanes, into *lanes (host int32). */
+swift_status swift_plan_get_lanes(swift_plan plan, int32_t* lanes);
 
 /* Capture one forward call on `batch` (all its levels) into a CUDA graph
  * owned by the plan; swift_plan_replay then re-runs it with one graph

@@ -195,6 +195,17 @@ class Plan:
         """Skew (1..16) of the persistent schedule's work order."""
         check(lib.swift_plan_set_skew(self._h, int(skew)), "swift_plan_set_skew")
 
+    def set_lanes(self, lanes: int):
+        """Lanes (1 or 2) that the plan's FP32 forward calls spread their
+        launches over: the call's stream and one auxiliary stream."""
+        check(lib.swift_plan_set_lanes(self._h, int(lanes)), "swift_plan_set_lanes")
+
+    @property
+    def lanes(self) -> int:
+        v = C.c_int32(0)
+        check(lib.swift_plan_get_lanes(self._h, C.byref(v)), "swift_plan_get_lanes")
+        return int(v.value)
+
     def set_test_hold(self, window: int):
         """Test hook: the row items of ``window`` (its position in the
         persistent launch's window sequence) never report completion and the

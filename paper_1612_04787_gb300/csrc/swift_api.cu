@@ -47,8 +47,15 @@ struct swift_plan_s {
   int sched[kMaxLevels] = {};
   // streaming forward path: its workspace
   void* work = nullptr;
-  long long work_windows = 0;  // capacity (windows of the largest streamed size)
-  unsigned int* done = nullptr;  // [work_windows] per-window block counters of the streaming finalize (kept zero)
+  long long work_windows = 0;  // windows per slice with one lane (of the largest streamed size)
+  size_t work_per = 0;         // workspace bytes per window at the largest streamed size
+  unsigned int* done = nullptr;  // per-window block counters of the streaming finalize (kept zero)
+  // lanes: the streams one forward call spreads its launch units over (the
+  // call's stream and one auxiliary stream), each with its own part of the
+  // workspace; fork / join events order the auxiliary lane with the call
+  int lanes = 2;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // affine-warp forward and backward: allocated on first use
   void* bwork = nullptr;
   long long bwork_windows = 0;
@@ -96,6 +103,27 @@ bool has_persistent(int n) { return n == 64 || n == 128 || n == 256; }
 int persist_ring(int skew) { return 5 * skew + 4; }
 constexpr int kMaxSkew = 16;
 constexpr int kSkews[] = {4, 8, 12, 16};
+// lanes of a forward call: windows per streaming slice and the byte stride of
+// the lanes' workspace parts (256-aligned: the carve aligns within a part)
+constexpr int kMaxLanes = 2;
+long long lane_capacity(long long work_windows, int lanes) { return (work_windows + lanes - 1) / lanes; }
+size_t lane_stride(size_t per, long long capacity) {
+  return ((per * static_cast<size_t>(capacity) + 255) & ~static_cast<size_t>(255)) + 1024;
+}
+// the streams of one forward call: lane 0 is the call's stream; units (a
+// fused launch, a streaming slice) go to the lane with the least work queued
+struct Lanes {
+  cudaStream_t s[kMaxLanes] = {};
+  int n = 1;
+  double load[kMaxLanes] = {};
+};
+int lane_pick(Lanes& ls, double cost) {
+  int k = 0;
+  for (int i = 1; i < ls.n; ++i)
+    if (ls.load[i] < ls.load[k]) k = i;
+  ls.load[k] += cost;
+  return k;
+}
 }  // namespace
 
 static swift_status release(swift_plan p) {
@@ -122,6 +150,9 @@ static swift_status release(swift_plan p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->gw_acc) cudaFree(p->gw_acc);
   if (p->order_ev) cudaEventDestroy(p->order_ev);
+  if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  if (p->join_ev) cudaEventDestroy(p->join_ev);
+  if (p->aux) cudaStreamDestroy(p->aux);
   if (cur != p->device) cudaSetDevice(cur);
   delete p;
   return SWIFT_OK;
@@ -212,9 +243,17 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
   }
   if (per > 0) {
     p->work_windows = max_windows < kStreamSlice ? max_windows : kStreamSlice;
-    if (cudaMalloc(&p->work, per * p->work_windows + 4096) != cudaSuccess ||
-        cudaMalloc(&p->done, sizeof(unsigned int) * p->work_windows) != cudaSuccess ||
-        cudaMemset(p->done, 0, sizeof(unsigned int) * p->work_windows) != cudaSuccess) {
+    p->work_per = per;
+    // room for kMaxLanes lanes of lane_capacity windows each (at least the
+    // single-lane slice of work_windows)
+    const long long c = lane_capacity(p->work_windows, kMaxLanes);
+    const size_t bytes = kMaxLanes * lane_stride(per, c) + 4096;
+    if (cudaMalloc(&p->work, bytes) != cudaSuccess ||
+        cudaMalloc(&p->done, sizeof(unsigned int) * kMaxLanes * c) != cudaSuccess ||
+        cudaMemset(p->done, 0, sizeof(unsigned int) * kMaxLanes * c) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming) != cudaSuccess) {
       release(p);
       cudaGetLastError();
       return SWIFT_ERR_OOM;
@@ -308,8 +347,12 @@ static swift::MatchLaunch level_launch_forward(swift_plan plan, const swift_batc
   return L;
 }
 
-// Launch the windows of level l with the level's schedule (fused or streaming).
-static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, swift_result* out, cudaStream_t st) {
+// Launch the windows of level l with the level's schedule (fused or
+// streaming) over the call's lanes: each streaming slice (at most the lane
+// capacity) and each fused launch goes to the least-loaded lane, a slice in
+// that lane's part of the workspace.
+static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, swift_result* out, Lanes& ls) {
+  const cudaStream_t st = ls.s[0];
   int64_t B0 = 0, B = 0;
   level_range(batch, l, &B0, &B);
   if (B == 0) return SWIFT_OK;
@@ -334,16 +377,19 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
     return SWIFT_OK;
   }
   if (plan->sched[l] != SWIFT_SCHED_FUSED) {
-    for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
-      const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
-      swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
-      W.done = plan->done;
+    const long long cap = lane_capacity(plan->work_windows, ls.n);
+    const size_t stride = lane_stride(plan->work_per, cap);
+    for (long long b0 = 0; b0 < B; b0 += cap) {
+      const long long cnt = (B - b0) < cap ? (B - b0) : cap;
+      const int k = lane_pick(ls, static_cast<double>(cnt) * lv.n * lv.n);
+      swift::StreamWork W = swift::stream_carve(static_cast<unsigned char*>(plan->work) + k * stride, cap, lv.n, b0, cnt);
+      W.done = plan->done + k * cap;
       if (plan->timing) {
         const int set = plan->tcount++ % kTimingSets;
         plan->tkind[set] = 0;
         W.ev = plan->tev + 6 * set;
       }
-      if (swift::launch_stream(lv.n, plan->dtype, L, W, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+      if (swift::launch_stream(lv.n, plan->dtype, L, W, ls.s[k]) != cudaSuccess) return SWIFT_ERR_CUDA;
     }
     return SWIFT_OK;
   }
@@ -351,15 +397,16 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
                     (reinterpret_cast<uintptr_t>(ri.data) % 16) == 0 &&
                     (reinterpret_cast<uintptr_t>(mi.data) % 16) == 0 && ri.pitch % 16 == 0 &&
                     mi.pitch % 16 == 0 && ri.width % 16 == 0 && mi.width % 16 == 0;
+  const cudaStream_t fs = ls.s[lane_pick(ls, static_cast<double>(B) * lv.n * lv.n)];
   cudaEvent_t* ev = nullptr;
   if (plan->timing) {
     const int set = plan->tcount++ % kTimingSets;
     plan->tkind[set] = 1;
     ev = plan->tev + 6 * set;
-    cudaEventRecord(ev[0], st);
+    cudaEventRecord(ev[0], fs);
   }
-  if (swift::launch_forward(lv.n, plan->dtype, bulk, L, st) != cudaSuccess) return SWIFT_ERR_CUDA;
-  if (ev) cudaEventRecord(ev[1], st);
+  if (swift::launch_forward(lv.n, plan->dtype, bulk, L, fs) != cudaSuccess) return SWIFT_ERR_CUDA;
+  if (ev) cudaEventRecord(ev[1], fs);
   return SWIFT_OK;
 }
 
@@ -459,20 +506,35 @@ static swift_status run_persistent(swift_plan plan, const swift_batch* batch, un
 static swift_status match_launches(swift_plan plan, const swift_batch* batch, swift_result* out, cudaStream_t st) {
   if (batch->affine) return warp_forward(plan, batch, out, st);
   const int used_levels = batch_levels(plan, batch);
+  Lanes ls;
+  ls.s[0] = st;
+  ls.s[1] = plan->aux;
+  // FP32 forward calls spread over the lanes; the auxiliary lane first waits
+  // for what the call's stream has queued (the fork) and the call's stream
+  // finally waits for the auxiliary lane (the join), so the call stays one
+  // ordered unit of its stream (and of a captured graph)
+  ls.n = (plan->prec == SWIFT_PREC_FP32 && plan->lanes > 1 && plan->aux) ? plan->lanes : 1;
+  if (ls.n > 1 && (cudaEventRecord(plan->fork_ev, st) != cudaSuccess ||
+                   cudaStreamWaitEvent(plan->aux, plan->fork_ev, 0) != cudaSuccess)) {
+    cudaGetLastError();
+    return SWIFT_ERR_CUDA;
+  }
   unsigned int mask = 0;
-  for (int l = 0; l < used_levels; ++l) {
+  swift_status e = SWIFT_OK;
+  for (int l = 0; l < used_levels && e == SWIFT_OK; ++l) {
     if (plan->prec == SWIFT_PREC_FP32 && plan->sched[l] == SWIFT_SCHED_PERSISTENT && has_persistent(plan->levels[l].n) &&
         batch->n_windows < (1ll << 24)) {
       mask |= 1u << l;
       continue;
     }
-    const swift_status e = run_level(plan, batch, l, out, st);
-    if (e != SWIFT_OK) return e;
+    e = run_level(plan, batch, l, out, ls);
   }
-  if (mask) {
-    const swift_status e = run_persistent(plan, batch, mask, out, st);
-    if (e != SWIFT_OK) return e;
+  if (e == SWIFT_OK && mask) e = run_persistent(plan, batch, mask, out, st);
+  if (ls.n > 1 && (cudaEventRecord(plan->join_ev, plan->aux) != cudaSuccess ||
+                   cudaStreamWaitEvent(st, plan->join_ev, 0) != cudaSuccess) && e == SWIFT_OK) {
+    e = SWIFT_ERR_CUDA;
   }
+  if (e != SWIFT_OK) return e;
   if (cudaGetLastError() != cudaSuccess) return SWIFT_ERR_CUDA;
   return SWIFT_OK;
 }
@@ -710,9 +772,11 @@ extern "C" swift_status swift_plan_autotune(swift_plan plan, const swift_batch* 
     for (int s : {SWIFT_SCHED_FUSED, SWIFT_SCHED_STREAM}) {
       if (s == SWIFT_SCHED_FUSED && !has_fused(plan->levels[l].n)) continue;
       plan->sched[l] = s;
-      if ((e = run_level(plan, batch, l, out, st)) != SWIFT_OK) break;  // warm-up
+      Lanes one;
+      one.s[0] = st;
+      if ((e = run_level(plan, batch, l, out, one)) != SWIFT_OK) break;  // warm-up
       cudaEventRecord(e0, st);
-      for (int rep = 0; rep < 3 && e == SWIFT_OK; ++rep) e = run_level(plan, batch, l, out, st);
+      for (int rep = 0; rep < 3 && e == SWIFT_OK; ++rep) e = run_level(plan, batch, l, out, one);
       cudaEventRecord(e1, st);
       float ms = 0.f;
       if (e != SWIFT_OK) break;
@@ -751,6 +815,17 @@ extern "C" swift_status swift_plan_autotune(swift_plan plan, const swift_batch* 
   for (int l = 0; l < used; ++l)
     plan->sched[l] = best_persist && has_persistent(plan->levels[l].n) ? SWIFT_SCHED_PERSISTENT : per_level[l];
   plan->pskew = best_skew;
+  // (c) one lane or two for the chosen schedules
+  if (e == SWIFT_OK && plan->aux && plan->prec == SWIFT_PREC_FP32) {
+    float lane_ms[kMaxLanes + 1] = {};
+    int best_lanes = plan->lanes;
+    for (int k = 1; k <= kMaxLanes && e == SWIFT_OK; ++k) {
+      plan->lanes = k;
+      e = time_calls(plan, batch, out, st, e0, e1, &lane_ms[k]);
+      if (e == SWIFT_OK && (k == 1 || lane_ms[k] < lane_ms[best_lanes])) best_lanes = k;
+    }
+    plan->lanes = best_lanes;
+  }
   if (chosen)
     for (int l = 0; l < used; ++l) chosen[l] = plan->sched[l];
   cudaEventDestroy(e0);
@@ -816,6 +891,19 @@ extern "C" swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enabl
 extern "C" swift_status swift_plan_set_skew(swift_plan plan, int32_t skew) {
   if (!plan || skew < 1 || skew > kMaxSkew) return SWIFT_ERR_INVALID_ARG;
   plan->pskew = skew;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_lanes(swift_plan plan, int32_t lanes) {
+  if (!plan || lanes < 1 || lanes > kMaxLanes) return SWIFT_ERR_INVALID_ARG;
+  if (lanes > 1 && !plan->aux) return SWIFT_ERR_INVALID_ARG;  // no streaming workspace: nothing to spread
+  plan->lanes = lanes;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_get_lanes(swift_plan plan, int32_t* lanes) {
+  if (!plan || !lanes) return SWIFT_ERR_INVALID_ARG;
+  *lanes = plan->aux ? plan->lanes : 1;
   return SWIFT_OK;
 }
 
