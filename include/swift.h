@@ -338,8 +338,12 @@ swift_status swift_plan_replay(swift_plan plan, void* stream);
  * starts over.  Slots: 0 statistics, 1 row transforms, 2 column
  * transforms + whitening, 3 inverse row transforms, 4 finalize (the
  * streaming schedule, and the same five kernels of the BF16X2 / FP16X2
- * forms), 5 fused kernel, 6 persistent launch (its clearing of the work
- * queue included), 7 unused.  kernel_ms and launches are host arrays of 8. */
+ * forms; a streaming slice whose finalize is folded into its inverse rows --
+ * n <= 256, exclusion radius below 8 px -- launches no finalize kernel and
+ * counts none), 5 fused kernel, 6 persistent launch (its clearing of the
+ * work queue included), 7 unused.  kernel_ms and launches are host arrays of
+ * 8.  With two lanes (swift_plan_set_lanes) launches of different slices
+ * overlap, so each launch's time includes the GPU it shared. */
 swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
 
 /* Test hook for the bounded-wait failure path (not for production use).

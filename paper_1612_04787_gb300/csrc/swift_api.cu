@@ -73,7 +73,8 @@ struct swift_plan_s {
   bool test_stale_ok = false;  // swift_plan_set_test_stale_status
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // [kTimingSets][6]
-  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch
+  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch, 2 = persistent
+                                // launch, 3 = streaming set whose finalize is folded (no fifth kernel)
   int tcount = 0;               // sets used since the last read
   // one captured forward call (swift_plan_capture / swift_plan_replay)
   cudaGraph_t graph = nullptr;
@@ -386,7 +387,8 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
       W.done = plan->done + k * cap;
       if (plan->timing) {
         const int set = plan->tcount++ % kTimingSets;
-        plan->tkind[set] = 0;
+        // the launcher folds the finalize into the inverse rows for n <= 256 and radii below 8 px
+        plan->tkind[set] = (lv.n <= 256 && L.radius2 < 64.f) ? 3 : 0;
         W.ev = plan->tev + 6 * set;
       }
       if (swift::launch_stream(lv.n, plan->dtype, L, W, ls.s[k]) != cudaSuccess) return SWIFT_ERR_CUDA;
@@ -966,12 +968,15 @@ extern "C" swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, in
   const int used = plan->tcount < kTimingSets ? plan->tcount : kTimingSets;
   for (int set = 0; set < used; ++set) {
     cudaEvent_t* ev = plan->tev + 6 * set;
-    const int nk = plan->tkind[set] == 0 ? 5 : 1;  // 1: fused launch, 2: persistent launch
+    const int kind = plan->tkind[set];
+    const bool streaming = kind == 0 || kind == 3;
+    const int nk = streaming ? 5 : 1;  // 1: fused launch, 2: persistent launch
     if (cudaEventSynchronize(ev[nk]) != cudaSuccess) return SWIFT_ERR_CUDA;
     for (int k = 0; k < nk; ++k) {
+      if (kind == 3 && k == 4) continue;  // no finalize kernel ran between these events
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return SWIFT_ERR_CUDA;
-      const int slot = plan->tkind[set] == 0 ? k : (plan->tkind[set] == 1 ? 5 : 6);
+      const int slot = streaming ? k : (kind == 1 ? 5 : 6);
       kernel_ms[slot] += ms;
       launches[slot] += 1;
     }
