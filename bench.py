@@ -1302,7 +1302,10 @@ def main():
         dom_name = (TC_KERNEL_NAMES if tensor else kernel_names(W.dominant_n))[dom]
     else:
         dom_name, achieved, shares, windows_per_launch = "pipeline (graph replay)", step_tflops, None, W.windows
-    traffic = recorded_traffic(f"{dom_name}<{W.dominant_n}>", windows_per_launch)
+    # traffic records are per kernel, window size and input type (a row kernel
+    # reads 1-byte or 4-byte pixels)
+    in_key = "u8" if W.config.get("input") == "uint8" else "f32"
+    traffic = recorded_traffic(f"{dom_name}<{W.dominant_n},{in_key}>", windows_per_launch)
     if tensor:
         pk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
         roofline = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
