@@ -315,7 +315,7 @@ class Sections:
         self.horg = torch.from_numpy(self.org).pin_memory()
         self.hout = [torch.empty((self.B1, 8), dtype=torch.int32).pin_memory() for _ in self.secs]
         self.flops = flops_per_pair(self.n) * self.windows
-        self.launches_per_step = 4 * self.plan.lanes * len(self.secs)
+        self.launches_per_step = 3 * self.plan.lanes * len(self.secs)
         self.config = {"window": self.n, "windows_per_step": self.windows, "section_pairs_per_step": pairs,
                        "whiten_exponent": self.w, "apod": "hann", "snr_exclusion_radius": self.r, "input": "uint8",
                        "lanes": self.plan.lanes}
@@ -482,12 +482,13 @@ class Pyramid:
         self.cap_stream.synchronize()
         self.flops = sum(flops_per_pair(lv.n) * int((self.lvl == k).sum()) for k, lv in enumerate(self.levels))
         # the streaming schedule walks each level's range in slices of
-        # min(max_windows, 2048) / lanes windows, four kernels a slice (the
-        # finalize folded into the inverse rows for exclusion radii below 8 px)
+        # min(max_windows, 2048) / lanes windows, three kernels a slice up to
+        # 256 x 256 (the statistics folded into the rows and the column pairs,
+        # the finalize into the inverse rows for exclusion radii below 8 px)
         counts = [self.offs[k + 1] - self.offs[k] for k in range(len(self.levels))]
         self.lanes = self.plan.lanes
         cap = -(-min(self.windows, 2048) // self.lanes)
-        self.launches_per_step = int(sum(1 if c == "fused" else 4 * -(-int(n) // cap)
+        self.launches_per_step = int(sum(1 if c == "fused" else 3 * -(-int(n) // cap)
                                       for c, n in zip(self.chosen, counts) if c != "persistent")
                                   + (1 if "persistent" in self.chosen else 0))
         self.h = [(torch.from_numpy(x[0]).pin_memory(), torch.from_numpy(x[1]).pin_memory()) for x in self.imgs]
@@ -540,7 +541,12 @@ class Patches:
             self.plan.set_lanes(lanes)
         self.out = torch.empty((count, 8), dtype=torch.int32, device=dev)
         self.flops = flops_per_pair(n) * count
-        self.launches_per_step = 5 * ((count + 2047) // 2048)
+        # used only when no timing events count them: tensor-core forms five
+        # kernels per slice of 2048, FP32 three per slice of 2048 / lanes
+        if precision == "fp32":
+            self.launches_per_step = 3 * -(-count // -(-min(count, 2048) // self.plan.lanes))
+        else:
+            self.launches_per_step = 5 * -(-count // 2048)
         self.hout = torch.empty((count, 8), dtype=torch.int32).pin_memory()
         self.config = {"window": n, "windows_per_step": count, "input": "float32", "precision": precision,
                        "whiten_exponent": self.w}
@@ -689,7 +695,8 @@ class Whitening:
         self.out = torch.empty((self.windows, 8), dtype=torch.int32, device=dev)
         self.hout = torch.empty((self.windows, 8), dtype=torch.int32).pin_memory()
         self.flops = flops_per_pair(self.n) * self.windows
-        self.launches_per_step = 5 * E * -(-count // 2048)  # each exponent's range in slices of 2048
+        # each exponent's range in slices of 2048 / lanes, three kernels a slice
+        self.launches_per_step = 3 * E * -(-count // -(-min(self.windows, 2048) // self.plan.lanes))
         self.count = count
         self.config = {"window": 256, "windows_per_step": self.windows, "pairs": count, "exponents": self.exps,
                        "input": "uint8"}

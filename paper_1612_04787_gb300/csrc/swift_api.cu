@@ -39,6 +39,7 @@ struct swift_plan_s {
   int64_t max_windows = 0;
   int device = 0;
   float* taper[kMaxLevels] = {};
+  float* ahat[kMaxLevels] = {};  // DFT of each level's 1D taper (swift::launch_taper_spectrum)
   double inv_sum_a[kMaxLevels] = {};
   float2* twiddle[kNumSizes] = {};
   // tensor-core precision variant: fragment and twiddle tables per window size
@@ -73,8 +74,9 @@ struct swift_plan_s {
   bool test_stale_ok = false;  // swift_plan_set_test_stale_status
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // [kTimingSets][6]
-  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set, 1 = fused launch, 2 = persistent
-                                // launch, 3 = streaming set whose finalize is folded (no fifth kernel)
+  int* tkind = nullptr;         // [kTimingSets] 0 = streaming set (five kernels), 1 = fused launch,
+                                // 2 = persistent launch, 8 | bits = FP32 streaming set (bit 1: no
+                                // finalize kernel, bit 2: no statistics kernel)
   int tcount = 0;               // sets used since the last read
   // one captured forward call (swift_plan_capture / swift_plan_replay)
   cudaGraph_t graph = nullptr;
@@ -132,8 +134,10 @@ static swift_status release(swift_plan p) {
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != p->device) cudaSetDevice(p->device);
-  for (int l = 0; l < kMaxLevels; ++l)
+  for (int l = 0; l < kMaxLevels; ++l) {
     if (p->taper[l]) cudaFree(p->taper[l]);
+    if (p->ahat[l]) cudaFree(p->ahat[l]);
+  }
   for (int i = 0; i < kNumSizes; ++i) {
     if (p->twiddle[i]) cudaFree(p->twiddle[i]);
     if (p->tc_tab[i]) cudaFree(p->tc_tab[i]);
@@ -205,8 +209,14 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
       af[k] = static_cast<float>(a[k]);
     }
     p->inv_sum_a[l] = 1.0 / (s * s);
+    // the taper's transform, computed on the device from the FP32 taper (the
+    // allocation-free path computes it with the same kernel)
     if (cudaMalloc(&p->taper[l], sizeof(float) * n) != cudaSuccess ||
-        cudaMemcpy(p->taper[l], af, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(p->taper[l], af, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&p->ahat[l], sizeof(float) * n) != cudaSuccess ||
+        swift::launch_taper_spectrum(n, levels[l].apod, levels[l].tukey_alpha, p->taper[l], p->ahat[l], nullptr) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(nullptr) != cudaSuccess) {
       release(p);
       cudaGetLastError();
       return SWIFT_ERR_OOM;
@@ -325,6 +335,7 @@ static swift::MatchLaunch level_launch_forward(swift_plan plan, const swift_batc
   L.radius2 = static_cast<float>(floor(r2));
   L.inv_sum_a = plan->inv_sum_a[l];
   L.taper = plan->taper[l];
+  L.ahat = plan->ahat[l];
   L.twiddle = plan->twiddle[size_slot(lv.n)];
   L.stall_tx = plan->test_stall ? 16u : 0u;
   L.stale_ok = plan->test_stale_ok ? 1 : 0;
@@ -388,7 +399,9 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
       if (plan->timing) {
         const int set = plan->tcount++ % kTimingSets;
         // the launcher folds the finalize into the inverse rows for n <= 256 and radii below 8 px
-        plan->tkind[set] = (lv.n <= 256 && L.radius2 < 64.f) ? 3 : 0;
+        // (kind bit 1), and the statistics into the rows for n <= 256 (kind bit 2)
+        plan->tkind[set] = 8 | ((lv.n <= 256 && L.radius2 < 64.f) ? 1 : 0) |
+                           (swift::stream_stats_folded(lv.n, L) ? 2 : 0);
         W.ev = plan->tev + 6 * set;
       }
       if (swift::launch_stream(lv.n, plan->dtype, L, W, ls.s[k]) != cudaSuccess) return SWIFT_ERR_CUDA;
@@ -969,11 +982,12 @@ extern "C" swift_status swift_plan_timings(swift_plan plan, float* kernel_ms, in
   for (int set = 0; set < used; ++set) {
     cudaEvent_t* ev = plan->tev + 6 * set;
     const int kind = plan->tkind[set];
-    const bool streaming = kind == 0 || kind == 3;
+    const bool streaming = kind == 0 || (kind & 8);
     const int nk = streaming ? 5 : 1;  // 1: fused launch, 2: persistent launch
     if (cudaEventSynchronize(ev[nk]) != cudaSuccess) return SWIFT_ERR_CUDA;
     for (int k = 0; k < nk; ++k) {
-      if (kind == 3 && k == 4) continue;  // no finalize kernel ran between these events
+      // no finalize / statistics kernel ran between these events
+      if (((kind & 8) && (kind & 1) && k == 4) || ((kind & 8) && (kind & 2) && k == 0)) continue;
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return SWIFT_ERR_CUDA;
       const int slot = streaming ? k : (kind == 1 ? 5 : 6);

@@ -72,6 +72,7 @@ struct MatchLaunch {
   double inv_sum_a;                  // 1 / sum over the window of the 2D taper
   const float* taper;                // [n] 1D taper
   const float2* twiddle;             // [R2][R1] forward W_n^{j m}
+  const float* ahat = nullptr;       // [n] DFT of the 1D taper (real: the taper is symmetric), or null
   swift_result* out;                 // [B]
   const int* pre_status = nullptr;   // [slice] status decided before the statistics (or null)
   unsigned int stall_tx = 0;         // test hook: bytes the float row staging waits for that never arrive
@@ -89,7 +90,51 @@ struct StreamWork {
   cudaEvent_t* ev = nullptr; // host: 6 events recorded around the five kernels (timing), or null
   unsigned int* done = nullptr;  // [S] finished inverse-row blocks per window (zero between calls), or
                                  // null: the finalize then runs as a kernel of its own
+  float* rstat = nullptr;        // [S][n / RB][8] row-block statistics records (stream_carve)
 };
+
+// Whether a plain FP32 forward slice of n x n windows runs without the
+// statistics kernel: the row kernel records each block's sums and flatness,
+// and the column-pair kernel removes the means in the spectrum (needs the
+// taper's transform, MatchLaunch::ahat).
+inline bool stream_stats_folded(int n, const MatchLaunch& L) {
+  return n <= 256 && L.ahat != nullptr && L.pre_status == nullptr;
+}
+
+// The DFT of a level's 1D taper, Ahat[k] = sum_j a[j] cos(2 pi j k / n) (the
+// sine part vanishes: the periodic taper is symmetric), for k < n, into a
+// device array: closed forms for no taper (n at k = 0) and the Hann taper
+// (n / 2 at 0, -n / 4 at +-1, 0 elsewhere), else the FP32 sum over j in order
+// with cos from cospif.  One kernel on `stream`; the plan path and the
+// allocation-free path both call it, so their tables are equal.
+cudaError_t launch_taper_spectrum(int n, int apod, float alpha, const float* taper, float* out, cudaStream_t stream);
+// the same in one CTA (threads tid of nth); cos_tab: n floats of shared
+// memory; the taper must be visible to the whole CTA
+__device__ __forceinline__ void taper_spectrum(int n, int apod, float alpha, const float* taper, float* out,
+                                               float* cos_tab, int tid, int nth) {
+  const bool hann = apod == SWIFT_APOD_HANN || (apod == SWIFT_APOD_TUKEY && alpha >= 1.f);
+  if (apod == SWIFT_APOD_NONE || hann) {
+    for (int k = tid; k < n; k += nth) {
+      float v = 0.f;
+      if (apod == SWIFT_APOD_NONE) {
+        v = k == 0 ? static_cast<float>(n) : 0.f;
+      } else if (k == 0) {
+        v = 0.5f * static_cast<float>(n);
+      } else if (k == 1 || k == n - 1) {
+        v = -0.25f * static_cast<float>(n);
+      }
+      out[k] = v;
+    }
+    return;
+  }
+  for (int m = tid; m < n; m += nth) cos_tab[m] = cospif(2.f * static_cast<float>(m) / static_cast<float>(n));
+  __syncthreads();
+  for (int k = tid; k < n; k += nth) {
+    float acc = 0.f;
+    for (int j = 0; j < n; ++j) acc = fmaf(taper[j], cos_tab[(j * k) & (n - 1)], acc);
+    out[k] = acc;
+  }
+}
 
 // streaming forward path (swim_stream.cu): bytes of workspace per window, launch of one slice
 size_t stream_bytes_per_window(int n);
@@ -151,6 +196,7 @@ cudaError_t launch_tcf(int n, swift_dtype dtype, bool fp16, const MatchLaunch& L
 constexpr int kPersistMaxLevels = 16;
 constexpr int kPersistStages = 5;
 constexpr int kPersistPartStride = 24;  // u64 partials per window (NB3 <= 8, three each)
+constexpr int kPersistRowBlocks = 16;   // row blocks per window (n / RB <= 16 up to 256 x 256)
 constexpr int kCompactWindows = 2048;   // windows per compaction item
 struct PersistLevel {
   MatchLaunch L;  // the level's launch (tables, images, origins, results)
@@ -170,6 +216,7 @@ struct PersistLaunch {
   unsigned int* lcount;          // [kPersistMaxLevels] windows per level
   float4* stats;                 // [B]
   unsigned long long* part;      // [B][kPersistPartStride]
+  float* rstat;                  // [B][kPersistRowBlocks][8] row-block statistics records
   float2* zr;                    // ring [RING][nmax][nmax] row spectra
   float2* h;                     // ring [RING][nmax][nmax/2] inverse-column output
   int nmax;                      // largest window side of the launch

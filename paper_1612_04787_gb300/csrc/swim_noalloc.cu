@@ -21,7 +21,8 @@ namespace {
 
 // Static scratch shared by every call on a device (held until the process exits).
 constexpr size_t kNoAllocBytes = 24u << 20;  // 24 MiB
-constexpr size_t kTableBytes = 8192;         // taper (n floats, at 0) + twiddles (n complex, at 2048)
+constexpr size_t kTableBytes = 8192;         // taper (n floats, at 0), twiddles (n complex, at 2048) and
+                                             // the taper's transform (n floats, at 6144)
 constexpr size_t kDoneBytes = 2048;          // per-window finalize counters (512), after the tables; they
                                              // start at zero (static storage) and every call leaves them zero
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -49,13 +50,17 @@ long long capacity_for(int n) {
   return static_cast<long long>((kNoAllocBytes - kTableBytes - kDoneBytes - 4 * 256) / per);
 }
 
-// taper (n floats) and twiddle table (n complex, [m][j] with j < r1) of a level,
-// from the same definitions the plan path evaluates on the host
-__global__ void noalloc_tables_kernel(int n, int apod, double alpha, int r1, float* tap, float2* tw) {
+// taper (n floats), twiddle table (n complex, [m][j] with j < r1) and the
+// taper's transform (n floats) of a level, from the same definitions the plan
+// path evaluates (the transform with the same device function as its kernel)
+__global__ void noalloc_tables_kernel(int n, int apod, float alpha, int r1, float* tap, float2* tw, float* ahat) {
+  __shared__ float cos_tab[512];
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    tap[k] = static_cast<float>(swift::taper_value(n, apod, alpha, k));
+    tap[k] = static_cast<float>(swift::taper_value(n, apod, static_cast<double>(alpha), k));
     tw[k] = swift::twiddle_entry(n, r1, k);
   }
+  __syncthreads();
+  swift::taper_spectrum(n, apod, alpha, tap, ahat, cos_tab, threadIdx.x, blockDim.x);
 }
 
 }  // namespace
@@ -105,7 +110,8 @@ extern "C" swift_status swift_match_batch_noalloc(const swift_level* level, swif
   for (int k = 0; k < n; ++k) sum_a += swift::taper_value(n, lv.apod, lv.tukey_alpha, k);
   unsigned char* base = static_cast<unsigned char*>(scratch);
   noalloc_tables_kernel<<<1, 256, 0, st>>>(n, lv.apod, lv.tukey_alpha, r1, reinterpret_cast<float*>(base),
-                                           reinterpret_cast<float2*>(base + 2048));
+                                           reinterpret_cast<float2*>(base + 2048),
+                                           reinterpret_cast<float*>(base + 6144));
 
   swift::MatchLaunch L;
   L.ref = ri.data;
@@ -130,6 +136,7 @@ extern "C" swift_status swift_match_batch_noalloc(const swift_level* level, swif
   L.inv_sum_a = 1.0 / (sum_a * sum_a);
   L.taper = reinterpret_cast<const float*>(base);
   L.twiddle = reinterpret_cast<const float2*>(base + 2048);
+  L.ahat = reinterpret_cast<const float*>(base + 6144);
   L.out = out;
   swift::StreamWork W = swift::stream_carve(base + kTableBytes + kDoneBytes, capacity_for(n), n, 0, B);
   W.done = reinterpret_cast<unsigned int*>(base + kTableBytes);

@@ -45,7 +45,7 @@ size_t persist_bytes(int n_levels, long long B, int nmax, int ring) {
   const size_t nn = static_cast<size_t>(nmax) * nmax;
   return round256(sizeof(unsigned int) * (4 + kPersistMaxLevels)) + round256(sizeof(unsigned long long) * ring) +
          round256(sizeof(float4) * B) + round256(sizeof(unsigned long long) * kPersistPartStride * B) +
-         round256(sizeof(int) * n_levels * B) + round256(sizeof(float2) * nn * ring) +
+         round256(sizeof(float) * kPersistRowBlocks * 8 * B) + round256(sizeof(int) * n_levels * B) + round256(sizeof(float2) * nn * ring) +
          round256(sizeof(float2) * nn / 2 * ring);
 }
 
@@ -65,6 +65,8 @@ cudaError_t launch_persist(PersistLaunch P, void* work, swift_dtype dtype, cudaS
   p += round256(sizeof(float4) * P.B);
   P.part = reinterpret_cast<unsigned long long*>(p);
   p += round256(sizeof(unsigned long long) * kPersistPartStride * P.B);
+  P.rstat = reinterpret_cast<float*>(p);
+  p += round256(sizeof(float) * kPersistRowBlocks * 8 * P.B);
   P.lists = reinterpret_cast<int*>(p);
   p += round256(sizeof(int) * P.n_levels * P.B);
   const size_t nn = static_cast<size_t>(P.nmax) * P.nmax;

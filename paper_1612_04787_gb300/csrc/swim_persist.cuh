@@ -173,17 +173,19 @@ __device__ __forceinline__ void persist_slot_signal(unsigned long long* w, long 
 // The stage bodies are called, not inlined: each gets its own register
 // allocation (within the kernel's bound) instead of one allocation for the
 // union of all fifteen, which spilled heavily.
+// As in the streaming schedule (n <= 256, plain forward) the rows record each
+// block's statistics and the column pairs remove the means in the spectrum,
+// so the statistics item has no work of its own: it stays in the order as the
+// point where a window takes over its ring slot.
 template <int N, typename TIn>
-__device__ __noinline__ void persist_s0(const MatchLaunch* L, WinRef R) {
-  stats_stage<N, TIn>(*L, R);
-}
+__device__ __noinline__ void persist_s0(const MatchLaunch*, WinRef) {}
 template <int N, typename TIn>
 __device__ __noinline__ void persist_s1(const MatchLaunch* L, WinRef R, int sub) {
-  rows_stage<N, TIn>(*L, R, sub);
+  rows_stage<N, TIn, true>(*L, R, sub);
 }
 template <int N>
 __device__ __noinline__ void persist_s2(const MatchLaunch* L, WinRef R, int sub) {
-  cpair_stage<N>(*L, R, sub);
+  cpair_stage<N, true>(*L, R, sub);
 }
 template <int N>
 __device__ __noinline__ void persist_s3(const MatchLaunch* L, WinRef R, int sub) {
@@ -220,6 +222,7 @@ __device__ __forceinline__ void persist_stage(const PersistLaunch& P, const Matc
   R.part = P.part + kPersistPartStride * R.b;
   R.pre = nullptr;
   R.done = nullptr;  // the finalize is an item of its own
+  R.rstat = P.rstat + static_cast<long long>(kPersistRowBlocks) * 8 * R.b;
   if (!live) {
     // the launch aborted: no work; a finalize item reports the window
     if (stage == 4 && threadIdx.x == 0) {

@@ -37,10 +37,16 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
   // pass in registers); n = 512 keeps the per-column kernel (its pass B would
   // hold 2 x 32 complex values per thread)
   constexpr bool kPair = N <= 256;
-  static unsigned m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+  // n <= 256, plain forward: no statistics kernel (the row kernel records
+  // each block's sums and flatness, the column-pair kernel combines them and
+  // removes the means in the spectrum)
+  const bool fold_stats = kPair && stream_stats_folded(N, L) && W.rstat != nullptr;
+  static unsigned m1 = 0, m2 = 0, m3 = 0, m4 = 0, m5 = 0, m6 = 0;
   if ((e = smem_optin(stream_rows_kernel<N, TIn>, rows_smem<N, TIn>(), m1, dev)) != cudaSuccess) return e;
   if constexpr (kPair) {
+    if ((e = smem_optin(stream_rows_kernel<N, TIn, true>, rows_smem<N, TIn>(), m5, dev)) != cudaSuccess) return e;
     if ((e = smem_optin(stream_cpair_kernel<N>, cpair_smem<N>(), m2, dev)) != cudaSuccess) return e;
+    if ((e = smem_optin(stream_cpair_kernel<N, true>, cpair_smem<N>(), m6, dev)) != cudaSuccess) return e;
   } else {
     if ((e = smem_optin(stream_cols_kernel<N>, cols_smem<N>(), m2, dev)) != cudaSuccess) return e;
   }
@@ -50,12 +56,24 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
     if (W.ev) cudaEventRecord(W.ev[k], st);
   };
   mark(0);
-  stream_stats_kernel<N, TIn><<<S, 256, 0, st>>>(L, W);
+  if (!fold_stats) stream_stats_kernel<N, TIn><<<S, 256, 0, st>>>(L, W);
   mark(1);
-  stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+  if constexpr (kPair) {
+    if (fold_stats) {
+      stream_rows_kernel<N, TIn, true><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+    } else {
+      stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+    }
+  } else {
+    stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+  }
   mark(2);
   if constexpr (kPair) {
-    stream_cpair_kernel<N><<<S * PairGeom<N>::NB, PairGeom<N>::T, cpair_smem<N>(), st>>>(L, W);
+    if (fold_stats) {
+      stream_cpair_kernel<N, true><<<S * PairGeom<N>::NB, PairGeom<N>::T, cpair_smem<N>(), st>>>(L, W);
+    } else {
+      stream_cpair_kernel<N><<<S * PairGeom<N>::NB, PairGeom<N>::T, cpair_smem<N>(), st>>>(L, W);
+    }
   } else {
     stream_cols_kernel<N><<<S * G::NB2, G::T2, cols_smem<N>(), st>>>(L, W);
   }
@@ -76,9 +94,24 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
 
 }  // namespace
 
+// row blocks of a window (the row kernel's CTAs per window)
+size_t row_blocks(int n) {
+  switch (n) {
+    case 64:
+      return 64 / StreamGeom<64>::RB;
+    case 128:
+      return 128 / StreamGeom<128>::RB;
+    case 512:
+      return 512 / StreamGeom<512>::RB;
+    default:
+      return 256 / StreamGeom<256>::RB;
+  }
+}
+
 size_t stream_bytes_per_window(int n) {
   const size_t nn = static_cast<size_t>(n) * n;
-  return sizeof(float4) + sizeof(float2) * nn + sizeof(float2) * nn / 2 + 3 * sizeof(unsigned long long) * blocks3(n);
+  return sizeof(float4) + sizeof(float2) * nn + sizeof(float2) * nn / 2 + 3 * sizeof(unsigned long long) * blocks3(n) +
+         8 * sizeof(float) * row_blocks(n);
 }
 
 StreamWork stream_carve(void* base, long long capacity, int n, long long b0, long long count) {
@@ -92,6 +125,8 @@ StreamWork stream_carve(void* base, long long capacity, int n, long long b0, lon
   W.h = reinterpret_cast<float2*>(p);
   p += align256(sizeof(float2) * nn / 2 * capacity);
   W.part = reinterpret_cast<unsigned long long*>(p);
+  p += align256(3 * sizeof(unsigned long long) * blocks3(n) * capacity);
+  W.rstat = reinterpret_cast<float*>(p);
   W.b0 = b0;
   W.count = count;
   return W;
@@ -114,6 +149,23 @@ bool stream_radices(int n, int* r1, int* r2) {
     default:
       return false;
   }
+}
+
+namespace {
+__global__ void __launch_bounds__(256) taper_spectrum_kernel(int n, int apod, float alpha, const float* taper,
+                                                             float* out) {
+  __shared__ float cos_tab[512];
+  __shared__ float tap[512];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) tap[j] = taper[j];
+  __syncthreads();
+  taper_spectrum(n, apod, alpha, tap, out, cos_tab, threadIdx.x, blockDim.x);
+}
+}  // namespace
+
+cudaError_t launch_taper_spectrum(int n, int apod, float alpha, const float* taper, float* out, cudaStream_t stream) {
+  if (n < 2 || n > 512 || (n & (n - 1)) != 0) return cudaErrorInvalidValue;
+  taper_spectrum_kernel<<<1, 256, 0, stream>>>(n, apod, alpha, taper, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stream(int n, swift_dtype dtype, const MatchLaunch& L, const StreamWork& W, cudaStream_t st) {

@@ -31,6 +31,11 @@
 namespace swift {
 
 constexpr int kStatusSkip = kWindowOtherLevel;  // window of another level: no result written here
+// flags of a row-block statistics record (the row kernel's STATS mode)
+constexpr int kRowDiffM = 1;      // a moving pixel differs from the moving window's first pixel
+constexpr int kRowDiffR = 2;      // a reference pixel differs from the reference window's first pixel
+constexpr int kRowNonFinite = 4;  // a non-finite float pixel
+constexpr int kRowTimeout = 8;    // the block's staged rows never arrived
 
 template <int N>
 struct StreamGeom {
@@ -79,6 +84,8 @@ struct WinRef {
   unsigned long long* part = nullptr;  // [NB3][3]
   const int* pre = nullptr;            // status decided before the statistics, or null
   unsigned int* done = nullptr;        // finished inverse-row blocks of the window (finalize in K3), or null
+  float* rstat = nullptr;              // [n / RB][8] row-block statistics records: the sums of A m and
+                                       // A r as float pairs (hi, lo), the flags (as int bits), unused
 };
 
 template <int N>
@@ -91,6 +98,7 @@ __device__ __forceinline__ WinRef slice_ref(const MatchLaunch& L, const StreamWo
   R.part = W.part + 3 * s * StreamGeom<N>::NB3;
   R.pre = L.pre_status != nullptr ? L.pre_status + s : nullptr;
   R.done = W.done != nullptr ? W.done + s : nullptr;
+  R.rstat = W.rstat != nullptr ? W.rstat + s * (N / StreamGeom<N>::RB) * 8 : nullptr;
   return R;
 }
 
@@ -334,7 +342,25 @@ __device__ __forceinline__ void transpose16_u8(uint32_t (&w)[4], int L) {
   }
 }
 
-template <int N, typename TIn>
+// per-warp partials of a row block's statistics (STATS mode), in shared memory
+struct RowBlockSums {
+  float s[8][2];
+  int f[8];
+};
+__device__ __forceinline__ RowBlockSums& row_block_sums() {
+  __shared__ RowBlockSums rbs;
+  return rbs;
+}
+
+// STATS (plain forward, n <= 256): no statistics kernel ran.  The block
+// checks the window's level and bounds itself (block 0 writes the status word;
+// the column-pair kernel sets the final one), transforms the rows of the
+// tapered windows A m and A r without their means, and records in R.rstat[rb]
+// its sums of A m and A r (float pairs over the block's warps), and flags: bit 0 / 1
+// a pixel of the moving / reference rows differs from that window's first
+// pixel (so a window is flat when no block sets the bit), bit 2 a non-finite
+// float pixel.  The column-pair kernel removes the means in the spectrum.
+template <int N, typename TIn, bool STATS = false>
 __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R, int rb) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, RB = G::RB, RS = G::RS, T = G::T;
@@ -346,9 +372,14 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
   constexpr bool kShfl = N == 256 && sizeof(TIn) == 1;
   const long long b = R.b;
   const int tid = threadIdx.x;
-  const float4 st = load_stats(R);
-  if (stat_status(st) != SWIFT_WIN_OK) return;
-  {
+  float4 st = make_float4(0.f, 0.f, 0.f, 0.f);  // the means (none in STATS mode)
+  if constexpr (STATS) {
+    const int guard = launch_window_check(L, b, N);
+    if (rb == 0 && tid == 0) *R.stats = make_float4(0.f, 0.f, __int_as_float(guard), 0.f);
+    if (guard != SWIFT_WIN_OK) return;
+  } else {
+    st = load_stats(R);
+    if (stat_status(st) != SWIFT_WIN_OK) return;
     // the window's level and bounds, from the launch's own arrays: a status
     // word left by another call never makes this kernel read
     const int guard = launch_window_check(L, b, N);
@@ -387,6 +418,18 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
             __ldg(L.ref_origin + 2 * b + 1);
     mpitch = L.mov_pitch;
     rpitch = L.ref_pitch;
+  }
+  // STATS: the windows' first pixels (the reference's as the staged rows
+  // average a K-section model), which the block's pixels are compared with
+  float p0m = 0.f, p0r = 0.f;
+  if constexpr (STATS) {
+    p0m = load_px<TIn>(mbase);
+    float r0 = load_px<TIn>(rbase);
+    if (L.ref_count > 1) {
+      for (int k = 1; k < L.ref_count; ++k) r0 += load_px<TIn>(rbase + k * L.ref_stride);
+      r0 *= 1.0f / static_cast<float>(L.ref_count);
+    }
+    p0r = r0;
   }
   mbase += static_cast<long long>(rb * RB) * mpitch;
   rbase += static_cast<long long>(rb * RB) * rpitch;
@@ -430,6 +473,12 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
         if (tid == 0) {
           mbar_wait_bounded(mbar, 0);
           *R.stats = make_float4(0.f, 0.f, __int_as_float(SWIFT_WIN_TIMEOUT), 0.f);
+          if constexpr (STATS) {
+            // block 0 may write OK after this: the record carries the timeout
+            float* rec = R.rstat + 8 * rb;
+            rec[0] = rec[1] = rec[2] = rec[3] = 0.f;
+            rec[4] = __int_as_float(kRowTimeout);
+          }
         }
         return;
       }
@@ -474,6 +523,20 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
   const int line = tid / R2, j = tid % R2;
   const int y = rb * RB + line;
   float mv[R1], rv[R1];
+  int rflags = 0;  // STATS: this thread's record flags
+  if constexpr (STATS && kShfl) {
+    if (vec) {
+      // the thread's 16 bytes of each row against the first pixel replicated
+      const uint32_t rm = 0x01010101u * static_cast<uint32_t>(p0m), rr = 0x01010101u * static_cast<uint32_t>(p0r);
+      uint32_t dm = 0u, dr = 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        dm |= wm[q] ^ rm;
+        dr |= wr[q] ^ rr;
+      }
+      rflags = (dm ? kRowDiffM : 0) | (dr ? kRowDiffR : 0);
+    }
+  }
   if (kShfl && vec) {
     // lane j of the half-warp of row `line` receives x = j + 16 m, m = 0..15
     transpose16_u8(wm, j);
@@ -491,6 +554,17 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
       rv[m] = vec ? static_cast<float>(rstage[e]) : rfstage[e];
     }
   }
+  if constexpr (STATS) {
+    if (!(kShfl && vec)) {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) {
+        rflags |= (mv[m] != p0m ? kRowDiffM : 0) | (rv[m] != p0r ? kRowDiffR : 0);
+        if constexpr (sizeof(TIn) == 4) {
+          rflags |= (!(fabsf(mv[m]) <= 3.4e38f) || !(fabsf(rv[m]) <= 3.4e38f)) ? kRowNonFinite : 0;
+        }
+      }
+    }
+  }
   if (!vec) __syncthreads();  // rfstage aliases the slab written below
   {
     const float ay = tap[y];
@@ -504,7 +578,30 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
 #pragma unroll
     for (int m = 0; m < R1; ++m) {
       const float a = ay * tx[m];
-      v[m] = make_float2(a * (mv[m] - st.x), a * (rv[m] - st.y));
+      if constexpr (STATS) {
+        v[m] = make_float2(a * mv[m], a * rv[m]);
+      } else {
+        v[m] = make_float2(a * (mv[m] - st.x), a * (rv[m] - st.y));
+      }
+    }
+    if constexpr (STATS) {
+      // the block's sums of A m and A r: FP32 within a warp (positive terms
+      // for uint8 windows), FP64 over the warps after the barrier below
+      float sm = 0.f, sr = 0.f;
+#pragma unroll
+      for (int m = 0; m < R1; ++m) {
+        sm += v[m].x;
+        sr += v[m].y;
+      }
+      sm = warp_sum_f32(sm);
+      sr = warp_sum_f32(sr);
+      const int f = static_cast<int>(__reduce_or_sync(0xffffffffu, static_cast<unsigned>(rflags)));
+      if ((tid & 31) == 0) {
+        RowBlockSums& S = row_block_sums();
+        S.s[tid >> 5][0] = sm;
+        S.s[tid >> 5][1] = sr;
+        S.f[tid >> 5] = f;
+      }
     }
     dft<R1, -1>(v);
     float2* row = slab + line * RS;
@@ -512,6 +609,24 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
     for (int q = 0; q < R1; ++q) row[G::phys(j + R2 * q)] = v[q];
   }
   __syncthreads();
+  if constexpr (STATS) {
+    if (tid < 32) {
+      // warp 0: the warps' partials summed as float pairs (no FP64 on this
+      // GPU's slow unit), one 32-byte record
+      const RowBlockSums& S = row_block_sums();
+      const int lane = tid;
+      float hm = lane < T / 32 ? S.s[lane][0] : 0.f, lm = 0.f;
+      float hr = lane < T / 32 ? S.s[lane][1] : 0.f, lr = 0.f;
+      warp_sum_ff2(hm, lm);
+      warp_sum_ff2(hr, lr);
+      const int fl = static_cast<int>(__reduce_or_sync(0xffffffffu, lane < T / 32 ? static_cast<unsigned>(S.f[lane]) : 0u));
+      if (lane == 0) {
+        float* rec = R.rstat + 8 * rb;
+        *reinterpret_cast<float4*>(rec) = make_float4(hm, lm, hr, lr);
+        rec[4] = __int_as_float(fl);
+      }
+    }
+  }
   // pass B: thread (line, k1) -> X[k1 + R1 k2], written to Zr[y][kx]
 #pragma unroll
   for (int i = 0; i < KB; ++i) {
@@ -532,10 +647,10 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
   }
 }
 
-template <int N, typename TIn>
-__global__ void __launch_bounds__(256) stream_rows_kernel(const MatchLaunch L, const StreamWork W) {
+template <int N, typename TIn, bool STATS = false>
+__global__ void __launch_bounds__(256, N == 512 ? 1 : 4) stream_rows_kernel(const MatchLaunch L, const StreamWork W) {
   constexpr int NRB = N / StreamGeom<N>::RB;
-  rows_stage<N, TIn>(L, slice_ref<N>(L, W, blockIdx.x / NRB), blockIdx.x % NRB);
+  rows_stage<N, TIn, STATS>(L, slice_ref<N>(L, W, blockIdx.x / NRB), blockIdx.x % NRB);
 }
 
 // ---------------------------------------------------------------------------
@@ -746,11 +861,17 @@ __device__ __forceinline__ float whiten_scaled(float mag2, float half_w, float l
   return f;
 }
 
-template <int N>
+// CORRECT (after a STATS row kernel): the window's means and status come from
+// the row blocks' records, and the means are removed in the spectrum: the
+// transform of A (x - mu) is that of A x minus mu Ahat(ky) Ahat(kx), Ahat the
+// (real) DFT of the symmetric 1D taper (L.ahat).  A flat, non-finite or timed
+// out window gets its status word here and is left.
+template <int N, bool CORRECT = false>
 __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& R, int cb) {
   using P = PairGeom<N>;
   constexpr int R1 = P::R1, R2 = P::R2, CB = P::CB, T = P::T, TW = P::TW;
   constexpr int RB = P::TB / T;  // pass B rounds per thread
+  constexpr int NRB = N / StreamGeom<N>::RB;  // row blocks of a window
   const int tid = threadIdx.x;
   if (stat_status(load_stats(R)) != SWIFT_WIN_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -758,7 +879,23 @@ __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& 
   float2* slab2 = reinterpret_cast<float2*>(smem_raw);  // [N][CB]: G after pass B' (reuses slab)
   float4* xbuf = slab + N * CB;                          // [R1][R2]: block 0, lc = 0
   float2* twT = reinterpret_cast<float2*>(xbuf + N);     // [R1][TW]: W_n^(k1 n2)
+  float* ahat = reinterpret_cast<float*>(twT + R1 * TW);  // [N] (CORRECT)
+  __shared__ float c_mu[2];
+  __shared__ int c_status;
   for (int i = tid; i < N; i += T) twT[(i % R1) * TW + i / R1] = L.twiddle[i];
+  // CORRECT: the row-block records are requested first (warp 0, one record a
+  // lane) and combined after pass A, when they have arrived
+  float4 rec_s = make_float4(0.f, 0.f, 0.f, 0.f);  // (hi, lo) of the sums of A m and A r
+  unsigned rec_f = 0u;
+  if constexpr (CORRECT) {
+    static_assert(NRB <= 32, "one record per lane");
+    if (tid < NRB) {
+      const float* rec = R.rstat + 8 * tid;
+      rec_s = __ldcg(reinterpret_cast<const float4*>(rec));
+      rec_f = static_cast<unsigned>(__float_as_int(__ldcg(rec + 4)));
+    }
+    for (int i = tid; i < N; i += T) ahat[i] = L.ahat[i];
+  }
   // pass A: task (j, lc) takes rows y = j + R2 m of columns kx and n - kx
   const float2* zr = R.zr;
 #pragma unroll
@@ -786,7 +923,33 @@ __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& 
 #pragma unroll
     for (int q = 0; q < R1; ++q) slab[(j + R2 * q) * CB + lc] = make_float4(a[q].x, a[q].y, b[q].x, b[q].y);
   }
+  if constexpr (CORRECT) {
+    if (tid < 32) {
+      // the window's row-block records: float-pair sums (lanes without a
+      // record hold zeros), flags ORed
+      float hm = rec_s.x, lm = rec_s.y, hr = rec_s.z, lr = rec_s.w;
+      warp_sum_ff2(hm, lm);
+      warp_sum_ff2(hr, lr);
+      const unsigned fl = __reduce_or_sync(0xffffffffu, rec_f);
+      if (tid == 0) {
+        c_status = (fl & kRowTimeout) ? SWIFT_WIN_TIMEOUT
+                   : (fl & kRowNonFinite) ? SWIFT_WIN_NONFINITE
+                   : ((fl & (kRowDiffM | kRowDiffR)) != (kRowDiffM | kRowDiffR)) ? SWIFT_WIN_FLAT
+                                                                                  : SWIFT_WIN_OK;
+        // mean = (hi + lo) / sum A, the pair rounded once
+        const float inv = static_cast<float>(L.inv_sum_a);
+        c_mu[0] = fmaf(hm, inv, lm * inv);
+        c_mu[1] = fmaf(hr, inv, lr * inv);
+      }
+    }
+  }
   __syncthreads();
+  if constexpr (CORRECT) {
+    if (c_status != SWIFT_WIN_OK) {
+      if (cb == 0 && tid == 0) *R.stats = make_float4(0.f, 0.f, __int_as_float(c_status), 0.f);
+      return;
+    }
+  }
   const float half_w = -0.5f * L.w;
   // 2^lscale = 4^(w-1) / n^2
   const float lscale = 2.f * L.w - 2.f - 2.f * static_cast<float>(__ffs(N) - 1);
@@ -815,6 +978,34 @@ __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& 
     }
     dft<R2, -1>(a);
     dft<R2, -1>(b);
+    if constexpr (CORRECT) {
+      // a = 2 M, b = 2i R at ky = k1 + R1 k2: subtract 2 mu Ahat(ky) Ahat(kx)
+      const int kx = CB * cb + lc;
+      if (kx == 0) {
+        // packed columns: a = 2 (M0 + i Mh), b = 2i R0 - 2 Rh (kx = 0 and n/2)
+        const float am0 = 2.f * c_mu[0] * ahat[0], amh = 2.f * c_mu[0] * ahat[N / 2];
+        const float ar0 = 2.f * c_mu[1] * ahat[0], arh = 2.f * c_mu[1] * ahat[N / 2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const float ay = ahat[k1 + R1 * k2];
+          a[k2].x = fmaf(-am0, ay, a[k2].x);
+          a[k2].y = fmaf(-amh, ay, a[k2].y);
+          b[k2].y = fmaf(-ar0, ay, b[k2].y);
+          b[k2].x = fmaf(arh, ay, b[k2].x);
+        }
+      } else {
+        const float ax = ahat[kx];
+        if (ax != 0.f) {  // the Hann and untapered transforms vanish off a few bins
+          const float am = 2.f * c_mu[0] * ax, ar = 2.f * c_mu[1] * ax;
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const float ay = ahat[k1 + R1 * k2];
+            a[k2].x = fmaf(-am, ay, a[k2].x);
+            b[k2].y = fmaf(-ar, ay, b[k2].y);
+          }
+        }
+      }
+    }
     if (cb == 0 && lc == 0) {
       // columns 0 and n/2: separated after the barrier below
 #pragma unroll
@@ -898,9 +1089,9 @@ __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& 
   }
 }
 
-template <int N>
+template <int N, bool CORRECT = false>
 __global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch L, const StreamWork W) {
-  cpair_stage<N>(L, slice_ref<N>(L, W, blockIdx.x / PairGeom<N>::NB), blockIdx.x % PairGeom<N>::NB);
+  cpair_stage<N, CORRECT>(L, slice_ref<N>(L, W, blockIdx.x / PairGeom<N>::NB), blockIdx.x % PairGeom<N>::NB);
 }
 
 // ---------------------------------------------------------------------------
@@ -1423,7 +1614,7 @@ constexpr size_t cols_smem() {
 template <int N>
 constexpr size_t cpair_smem() {
   using P = PairGeom<N>;
-  return sizeof(float4) * N * P::CB + sizeof(float4) * N + sizeof(float2) * P::R1 * P::TW;
+  return sizeof(float4) * N * P::CB + sizeof(float4) * N + sizeof(float2) * P::R1 * P::TW + sizeof(float) * N;
 }
 template <int N>
 constexpr size_t peak_smem() {
