@@ -217,7 +217,7 @@ swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_
  * results.
  *
  * Limits: at most floor((24 MiB - 9216 B) / per-window bytes) windows per
- * call: 7 windows of 512 x 512, 31 of 256 x 256, 127 of 128 x 128, 511 of
+ * call: 7 windows of 512 x 512, 31 of 256 x 256, 127 of 128 x 128, 510 of
  * 64 x 64.  Larger
  * batches return SWIFT_ERR_CAPACITY before any work is queued; split them.
  *
@@ -368,9 +368,10 @@ swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enable);
 swift_status swift_plan_set_test_hold(swift_plan plan, int64_t window);
 
 /* Test hook for the window guard (not for production use).  While enabled,
- * the statistics kernel of the FP32 streaming schedule reports windows of
- * other levels as OK without reading them -- the state a raced or stale
- * workspace could leave.  The row kernels re-check every window's level and
+ * the statistics kernel of the FP32 streaming schedule (512 x 512 levels:
+ * smaller windows take their statistics in the row kernel, which derives the
+ * status word itself) reports windows of other levels as OK without reading
+ * them -- the state a raced or stale workspace could leave.  The row kernels re-check every window's level and
  * bounds from the batch's own arrays (swift_window_check) before turning an
  * origin into an address, so such a window is still skipped and its result
  * record is left as it was. */

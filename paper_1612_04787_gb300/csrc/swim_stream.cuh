@@ -884,7 +884,7 @@ __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& 
   __shared__ int c_status;
   for (int i = tid; i < N; i += T) twT[(i % R1) * TW + i / R1] = L.twiddle[i];
   // CORRECT: the row-block records are requested first (warp 0, one record a
-  // lane) and combined after pass A, when they have arrived
+  // lane) and combined during pass A, behind its column loads
   float4 rec_s = make_float4(0.f, 0.f, 0.f, 0.f);  // (hi, lo) of the sums of A m and A r
   unsigned rec_f = 0u;
   if constexpr (CORRECT) {
@@ -918,30 +918,31 @@ __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& 
         b[m] = make_float2(zk.x - zn.x, zk.y + zn.y);
       }
     }
+    if constexpr (CORRECT) {
+      if (r == 0 && tid < 32) {
+        // warp 0, while its column loads are in flight: the window's
+        // row-block records as float-pair sums (lanes without a record hold
+        // zeros), flags ORed
+        float hm = rec_s.x, lm = rec_s.y, hr = rec_s.z, lr = rec_s.w;
+        warp_sum_ff2(hm, lm);
+        warp_sum_ff2(hr, lr);
+        const unsigned fl = __reduce_or_sync(0xffffffffu, rec_f);
+        if (tid == 0) {
+          c_status = (fl & kRowTimeout) ? SWIFT_WIN_TIMEOUT
+                     : (fl & kRowNonFinite) ? SWIFT_WIN_NONFINITE
+                     : ((fl & (kRowDiffM | kRowDiffR)) != (kRowDiffM | kRowDiffR)) ? SWIFT_WIN_FLAT
+                                                                                    : SWIFT_WIN_OK;
+          // mean = (hi + lo) / sum A, the pair rounded once
+          const float inv = static_cast<float>(L.inv_sum_a);
+          c_mu[0] = fmaf(hm, inv, lm * inv);
+          c_mu[1] = fmaf(hr, inv, lr * inv);
+        }
+      }
+    }
     dft<R1, -1>(a);
     dft<R1, -1>(b);
 #pragma unroll
     for (int q = 0; q < R1; ++q) slab[(j + R2 * q) * CB + lc] = make_float4(a[q].x, a[q].y, b[q].x, b[q].y);
-  }
-  if constexpr (CORRECT) {
-    if (tid < 32) {
-      // the window's row-block records: float-pair sums (lanes without a
-      // record hold zeros), flags ORed
-      float hm = rec_s.x, lm = rec_s.y, hr = rec_s.z, lr = rec_s.w;
-      warp_sum_ff2(hm, lm);
-      warp_sum_ff2(hr, lr);
-      const unsigned fl = __reduce_or_sync(0xffffffffu, rec_f);
-      if (tid == 0) {
-        c_status = (fl & kRowTimeout) ? SWIFT_WIN_TIMEOUT
-                   : (fl & kRowNonFinite) ? SWIFT_WIN_NONFINITE
-                   : ((fl & (kRowDiffM | kRowDiffR)) != (kRowDiffM | kRowDiffR)) ? SWIFT_WIN_FLAT
-                                                                                  : SWIFT_WIN_OK;
-        // mean = (hi + lo) / sum A, the pair rounded once
-        const float inv = static_cast<float>(L.inv_sum_a);
-        c_mu[0] = fmaf(hm, inv, lm * inv);
-        c_mu[1] = fmaf(hr, inv, lr * inv);
-      }
-    }
   }
   __syncthreads();
   if constexpr (CORRECT) {

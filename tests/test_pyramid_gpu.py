@@ -170,15 +170,17 @@ def test_calls_on_two_streams_are_ordered_by_the_plan(pyramid):
 
 def test_stale_ok_status_of_another_level_is_skipped_by_the_row_guard():
     """The statistics kernel is made to report every window of another level
-    as OK (the state a raced or stale workspace could leave).  The row kernels
-    re-check each window's level from the batch's own arrays, so those windows
-    are skipped: every result equals the normal call's, bit for bit.  Every
-    origin here lies inside every level's images, so no read could leave an
-    image even without the guard (the test does not rely on it for that)."""
-    a, b = synth.em_section_pair(512, seed_content=61, seed_warp=62, seed_noise=(63, 64))
+    as OK (the state a raced or stale workspace could leave).  It runs for the
+    512 x 512 level (windows up to 256 x 256 take their statistics in the row
+    kernel, which derives the status itself).  The row kernels re-check each
+    window's level from the batch's own arrays, so those windows are skipped:
+    every result equals the normal call's, bit for bit.  Every origin here lies
+    inside every level's images, so no read could leave an image even without
+    the guard (the test does not rely on it for that)."""
+    a, b = synth.em_section_pair(1024, seed_content=61, seed_warp=62, seed_noise=(63, 64))
     imgs_a, imgs_b = [synth.box_downsample(a, 2), a], [synth.box_downsample(b, 2), b]
-    levels = [swift.Level(128, 0.65), swift.Level(256, 0.8)]
-    o = synth.grid_origins(256, 128, 32)  # origins in [0, 128]: inside 256^2 for n = 128 and 512^2 for n = 256
+    levels = [swift.Level(128, 0.65), swift.Level(512, 0.8)]
+    o = synth.grid_origins(256, 128, 32)  # origins in [0, 128]: inside 512^2 for n = 128 and 1024^2 for n = 512
     org = np.concatenate([o, o]).astype(np.int32)
     lvl = np.concatenate([np.zeros(len(o), np.int32), np.ones(len(o), np.int32)])
     T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)  # noqa: E731
