@@ -257,12 +257,15 @@ swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, con
  *               memory of one CTA (64 x 64) or of a cluster of 2 (128 x 128)
  *               or 8 (256 x 256) CTAs, with the row/column redistributions
  *               through distributed shared memory
- *   STREAM      four or five kernels per slice of a level's windows
- *               (statistics, rows, column pairs, inverse rows; a finalize
- *               kernel only for exclusion radii of 8 px and more, else the
- *               last inverse-row block of each window finalizes it) of
- *               independent CTAs passing each window's intermediates through
- *               the plan's workspace
+ *   STREAM      kernels of independent CTAs per slice of a level's windows,
+ *               passing each window's intermediates through the plan's
+ *               workspace.  Up to 256 x 256 three: rows (each row block
+ *               records its sums and flatness), column pairs (the records
+ *               combined, the means removed in the spectrum, the whitening)
+ *               and inverse rows (the last block of each window finalizes
+ *               it), plus a finalize kernel for exclusion radii of 8 px and
+ *               more; 512 x 512 five (statistics, rows, columns, inverse
+ *               rows, finalize)
  *   PERSISTENT  the same five steps as work items of ONE kernel for every
  *               level that has this schedule: CTAs claim items in a fixed
  *               order from a queue and wait (bounded) for the items they
