@@ -209,8 +209,10 @@ swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_
  * path needs (window statistics, row spectra, whitened inverse-column data,
  * the match response) lives in one 24 MiB file-scope device array that every
  * GPU which loads the library holds until the process exits.  At every call
- * a small kernel on `stream` computes the taper and twiddle tables of `level`
- * straight into that array (no host buffer is read).  The paper has no
+ * a small kernel on `stream` computes the taper, twiddle and taper-transform
+ * tables of `level` straight into that array (no host buffer is read), so a
+ * call can be captured into a CUDA graph and replayed (after the set-up call
+ * below).  The paper has no
  * counterpart: this is a
  * deployment variant of swift_match_batch for a single level (batch->level
  * must be NULL); it runs the same streaming kernels and gives the same
@@ -229,7 +231,8 @@ swift_status swift_match_batch(swift_plan plan, const swift_batch* batch, swift_
  * same process.
  *
  * Sharing: all calls on a device use the same array and it keeps the last
- * call's contents (nothing in it has to start at zero).  Calls that overlap
+ * call's contents (its per-window finalize counters start at zero and every
+ * call leaves them at zero; nothing else in it has to hold any value).  Calls that overlap
  * on the GPU (different streams, or different host threads without ordering)
  * race on it and corrupt each other's results; order them on one stream. */
 swift_status swift_match_batch_noalloc(const swift_level* level, swift_dtype in, const swift_batch* batch,

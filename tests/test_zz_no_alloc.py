@@ -126,3 +126,33 @@ def test_noalloc_64_without_taper_matches_plan_path():
         assert noalloc_match(lv, "u8", ta, tb, tro, tmo, out) == _lib.SWIFT_OK
         torch.cuda.synchronize()
         assert_close(swift.decode(out), want)
+
+
+def test_noalloc_call_replays_from_a_captured_graph():
+    """Every call builds its tables on the device (no host buffer), so a call
+    can be captured into a CUDA graph: each replay gives the direct call's
+    records bit for bit, also after the scratch held another level's tables."""
+    a, b = synth.em_section_pair(1024, seed_content=81, seed_warp=82, seed_noise=(83, 84))
+    ta, tb = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    ro = synth.random_origins(20, 1024, 1024, 256, seed=85)
+    mo = np.clip(ro + np.random.default_rng(86).integers(-8, 9, ro.shape), 0, 768).astype(np.int32)
+    tro, tmo = torch.from_numpy(ro).to(DEV), torch.from_numpy(mo).to(DEV)
+    lv = swift.Level(256, 0.7, "tukey", 0.6, 3.0)
+    want = torch.empty((len(ro), 8), dtype=torch.int32, device=DEV)
+    assert noalloc_match(lv, "u8", ta, tb, tro, tmo, want) == _lib.SWIFT_OK
+    torch.cuda.synchronize()
+    out = torch.full_like(want, -1)
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream(device=DEV)
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=st):
+        code = noalloc_match(lv, "u8", ta, tb, tro, tmo, out)
+    assert code == _lib.SWIFT_OK
+    for k in range(3):
+        out.fill_(-1)
+        if k == 1:  # another level's call in between rewrites the scratch's tables
+            other = torch.empty((4, 8), dtype=torch.int32, device=DEV)
+            assert noalloc_match(swift.Level(128, 0.3), "u8", ta, tb, tro[:4], tmo[:4], other) == _lib.SWIFT_OK
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, want), k
