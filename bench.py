@@ -541,12 +541,10 @@ class Patches:
             self.plan.set_lanes(lanes)
         self.out = torch.empty((count, 8), dtype=torch.int32, device=dev)
         self.flops = flops_per_pair(n) * count
-        # used only when no timing events count them: tensor-core forms five
-        # kernels per slice of 2048, FP32 three per slice of 2048 / lanes
-        if precision == "fp32":
-            self.launches_per_step = 3 * -(-count // -(-min(count, 2048) // self.plan.lanes))
-        else:
-            self.launches_per_step = 5 * -(-count // 2048)
+        # used only when no timing events count them: slices of 2048 / lanes
+        # windows, FP32 three kernels a slice, the tensor-core forms five
+        slices = -(-count // -(-min(count, 2048) // self.plan.lanes))
+        self.launches_per_step = (3 if precision == "fp32" else 5) * slices
         self.hout = torch.empty((count, 8), dtype=torch.int32).pin_memory()
         self.config = {"window": n, "windows_per_step": count, "input": "float32", "precision": precision,
                        "whiten_exponent": self.w}
@@ -1206,7 +1204,7 @@ def main():
     # figures then come from a second timed region of the same steps with one
     # lane, and the headline value stays the two-lane region's
     timing = args.workload not in ("pyramid", "warp", "noise64")
-    lanes = W.plan.lanes if timing and args.precision == "fp32" else 1
+    lanes = W.plan.lanes if timing else 1
     separate = timing and lanes > 1
 
     def count_launches():

@@ -281,8 +281,9 @@ swift_status swift_match_backward(swift_plan plan, const swift_batch* batch, con
  *               may not be captured into a graph: swift_plan_capture makes an
  *               uncaptured call first)
  *   DEFAULT     FUSED for 64 x 64, STREAM for 128 x 128 and larger
- * An FP32 forward call spreads its launch units (each fused launch, each
- * streaming slice) over lanes: the call's stream and one auxiliary stream of
+ * A forward call spreads its launch units (each fused launch, each
+ * streaming slice, in every precision; the affine-warped forward excepted)
+ * over lanes: the call's stream and one auxiliary stream of
  * the plan, each lane with its own part of the workspace, so that one unit's
  * tail overlaps another's head.  The auxiliary lane waits for the work queued
  * on the call's stream before the call, and the call's stream waits for the
@@ -318,8 +319,8 @@ swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swif
  * 4, to hold in L2).  The autotuner sets it too. */
 swift_status swift_plan_set_skew(swift_plan plan, int32_t skew);
 
-/* Lanes of the plan's FP32 forward calls (1 or 2; default 2; the autotuner
- * sets it too).  With 1 every launch goes to the call's stream and a
+/* Lanes of the plan's forward calls (1 or 2; default 2; the autotuner sets
+ * it too; the affine-warped forward always uses one).  With 1 every launch goes to the call's stream and a
  * streaming slice holds up to min(max_windows, 2048) windows; with 2 the
  * slices hold up to half of that, alternating between the two lanes.  The
  * results do not depend on the lanes.  SWIFT_ERR_INVALID_ARG for other

@@ -196,7 +196,7 @@ class Plan:
         check(lib.swift_plan_set_skew(self._h, int(skew)), "swift_plan_set_skew")
 
     def set_lanes(self, lanes: int):
-        """Lanes (1 or 2) that the plan's FP32 forward calls spread their
+        """Lanes (1 or 2) that the plan's forward calls spread their
         launches over: the call's stream and one auxiliary stream."""
         check(lib.swift_plan_set_lanes(self._h, int(lanes)), "swift_plan_set_lanes")
 

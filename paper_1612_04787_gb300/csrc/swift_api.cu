@@ -374,17 +374,21 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
   const swift_image& mi = batch->mov[l];
   const swift::MatchLaunch L = level_launch_forward(plan, batch, l, out);
   if (plan->prec != SWIFT_PREC_FP32) {
+    // the tensor-core schedule's slices spread over the lanes like the FP32 ones
     const bool fp16 = plan->prec == SWIFT_PREC_FP16X2;
-    for (long long b0 = 0; b0 < B; b0 += plan->work_windows) {
-      const long long cnt = (B - b0) < plan->work_windows ? (B - b0) : plan->work_windows;
-      swift::StreamWork W = swift::stream_carve(plan->work, plan->work_windows, lv.n, b0, cnt);
+    const long long cap = lane_capacity(plan->work_windows, ls.n);
+    const size_t stride = lane_stride(plan->work_per, cap);
+    for (long long b0 = 0; b0 < B; b0 += cap) {
+      const long long cnt = (B - b0) < cap ? (B - b0) : cap;
+      const int k = lane_pick(ls, static_cast<double>(cnt) * lv.n * lv.n);
+      swift::StreamWork W = swift::stream_carve(static_cast<unsigned char*>(plan->work) + k * stride, cap, lv.n, b0, cnt);
       if (plan->timing) {
         const int set = plan->tcount++ % kTimingSets;
         plan->tkind[set] = 0;
         W.ev = plan->tev + 6 * set;
       }
       const swift::TcfLaunch T = swift::tcf_tables(plan->tc_tab[size_slot(lv.n)]);
-      if (swift::launch_tcf(lv.n, plan->dtype, fp16, L, W, T, st) != cudaSuccess) return SWIFT_ERR_CUDA;
+      if (swift::launch_tcf(lv.n, plan->dtype, fp16, L, W, T, ls.s[k]) != cudaSuccess) return SWIFT_ERR_CUDA;
     }
     return SWIFT_OK;
   }
@@ -524,11 +528,11 @@ static swift_status match_launches(swift_plan plan, const swift_batch* batch, sw
   Lanes ls;
   ls.s[0] = st;
   ls.s[1] = plan->aux;
-  // FP32 forward calls spread over the lanes; the auxiliary lane first waits
+  // forward calls spread over the lanes; the auxiliary lane first waits
   // for what the call's stream has queued (the fork) and the call's stream
   // finally waits for the auxiliary lane (the join), so the call stays one
   // ordered unit of its stream (and of a captured graph)
-  ls.n = (plan->prec == SWIFT_PREC_FP32 && plan->lanes > 1 && plan->aux) ? plan->lanes : 1;
+  ls.n = (plan->lanes > 1 && plan->aux) ? plan->lanes : 1;
   if (ls.n > 1 && (cudaEventRecord(plan->fork_ev, st) != cudaSuccess ||
                    cudaStreamWaitEvent(plan->aux, plan->fork_ev, 0) != cudaSuccess)) {
     cudaGetLastError();
@@ -831,7 +835,7 @@ extern "C" swift_status swift_plan_autotune(swift_plan plan, const swift_batch* 
     plan->sched[l] = best_persist && has_persistent(plan->levels[l].n) ? SWIFT_SCHED_PERSISTENT : per_level[l];
   plan->pskew = best_skew;
   // (c) one lane or two for the chosen schedules
-  if (e == SWIFT_OK && plan->aux && plan->prec == SWIFT_PREC_FP32) {
+  if (e == SWIFT_OK && plan->aux) {
     float lane_ms[kMaxLanes + 1] = {};
     int best_lanes = plan->lanes;
     for (int k = 1; k <= kMaxLanes && e == SWIFT_OK; ++k) {

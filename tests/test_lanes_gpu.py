@@ -106,3 +106,15 @@ def test_graph_replay_and_a_second_stream():
         plan.match(ta, tb, to, to, out=o, stream=s)
     torch.cuda.synchronize()
     assert all(torch.equal(o, want) for o in outs)
+
+
+def test_tensor_core_forms_on_two_lanes():
+    """The BF16X2 / FP16X2 schedules spread their slices over the lanes too
+    (40 windows: two slices of 20); the records equal one lane's."""
+    a, _ = synth.em_section_pair(1024, seed_content=241, seed_warp=242, seed_noise=(243, 244))
+    ref, mov, _ = synth.shifted_patches(a, 128, 40, seed=245)
+    for prec in ("bf16x2", "fp16x2"):
+        plan = swift.Plan([swift.Level(128, 0.65)], dtype="f32", precision=prec, max_windows=40)
+        one, two = _per_lanes(plan, T(ref), T(mov))
+        assert torch.equal(one, two), prec
+        assert (swift.decode(two)["status"] == 0).all()
