@@ -1306,7 +1306,9 @@ def main():
         shares = {k: round(v[0] / tot, 4) for k, v in kt.items()}
         dom_name = (TC_KERNEL_NAMES if tensor else kernel_names(W.dominant_n))[dom]
     else:
-        dom_name, achieved, shares, windows_per_launch = "pipeline (graph replay)", step_tflops, None, W.windows
+        # no per-kernel events: graph replays, or a step with the backward's kernels
+        label = "pipeline (graph replay)" if "graph" in W.config else "pipeline (whole step)"
+        dom_name, achieved, shares, windows_per_launch = label, step_tflops, None, W.windows
     # traffic records are per kernel, window size and input type (a row kernel
     # reads 1-byte or 4-byte pixels)
     in_key = "u8" if W.config.get("input") == "uint8" else "f32"
