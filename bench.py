@@ -63,6 +63,20 @@ def flops_per_pair(n: int) -> float:
     return 7.5 * m * math.log2(m) + 30.0 * m
 
 
+def stream_slices(count: int, max_windows: int, lanes: int) -> int:
+    """Streaming slices of a level's `count` windows in a plan for
+    `max_windows`: one lane takes slices of min(max_windows, 2048); two lanes
+    split the level into halves of at least 256 windows (at most the lane's
+    slice of min(max_windows, 2048), or half of it when that slice passes
+    2 GiB of workspace, which no bench plan does)."""
+    work = min(max_windows, 2048)
+    if lanes <= 1:
+        cap = work
+    else:
+        cap = min(max(-(-count // lanes), 256), work)
+    return -(-count // max(cap, 1))
+
+
 def kernel_flops(n: int) -> dict:
     """The same work split over the streaming kernels: rows = the row transforms
     of z = m' + i r' (one complex 2D half), cols = the forward column transforms
@@ -484,14 +498,13 @@ class Pyramid:
                                          stream=self.cap_stream, level_offsets=self.offs)
         self.cap_stream.synchronize()
         self.flops = sum(flops_per_pair(lv.n) * int((self.lvl == k).sum()) for k, lv in enumerate(self.levels))
-        # the streaming schedule walks each level's range in slices of
-        # min(max_windows, 2048) / lanes windows, three kernels a slice up to
-        # 256 x 256 (the statistics folded into the rows and the column pairs,
-        # the finalize into the inverse rows for exclusion radii below 8 px)
+        # the streaming schedule walks each level's range in slices (three
+        # kernels a slice up to 256 x 256: the statistics folded into the rows
+        # and the column pairs, the finalize into the inverse rows for
+        # exclusion radii below 8 px)
         counts = [self.offs[k + 1] - self.offs[k] for k in range(len(self.levels))]
         self.lanes = self.plan.lanes
-        cap = -(-min(self.windows, 2048) // self.lanes)
-        self.launches_per_step = int(sum(1 if c == "fused" else 3 * -(-int(n) // cap)
+        self.launches_per_step = int(sum(1 if c == "fused" else 3 * stream_slices(int(n), self.windows, self.lanes)
                                       for c, n in zip(self.chosen, counts) if c != "persistent")
                                   + (1 if "persistent" in self.chosen else 0))
         self.h = [(torch.from_numpy(x[0]).pin_memory(), torch.from_numpy(x[1]).pin_memory()) for x in self.imgs]
@@ -544,9 +557,9 @@ class Patches:
             self.plan.set_lanes(lanes)
         self.out = torch.empty((count, 8), dtype=torch.int32, device=dev)
         self.flops = flops_per_pair(n) * count
-        # used only when no timing events count them: slices of 2048 / lanes
-        # windows, FP32 three kernels a slice, the tensor-core forms five
-        slices = -(-count // -(-min(count, 2048) // self.plan.lanes))
+        # used only when no timing events count them: FP32 three kernels a
+        # slice, the tensor-core forms five
+        slices = stream_slices(count, count, self.plan.lanes)
         self.launches_per_step = (3 if precision == "fp32" else 5) * slices
         self.hout = torch.empty((count, 8), dtype=torch.int32).pin_memory()
         self.config = {"window": n, "windows_per_step": count, "input": "float32", "precision": precision,
@@ -696,8 +709,8 @@ class Whitening:
         self.out = torch.empty((self.windows, 8), dtype=torch.int32, device=dev)
         self.hout = torch.empty((self.windows, 8), dtype=torch.int32).pin_memory()
         self.flops = flops_per_pair(self.n) * self.windows
-        # each exponent's range in slices of 2048 / lanes, three kernels a slice
-        self.launches_per_step = 3 * E * -(-count // -(-min(self.windows, 2048) // self.plan.lanes))
+        # each exponent's range in its slices, three kernels a slice
+        self.launches_per_step = 3 * E * stream_slices(count, self.windows, self.plan.lanes)
         self.count = count
         self.config = {"window": 256, "windows_per_step": self.windows, "pairs": count, "exponents": self.exps,
                        "input": "uint8"}

@@ -320,11 +320,14 @@ swift_status swift_plan_autotune(swift_plan plan, const swift_batch* batch, swif
 swift_status swift_plan_set_skew(swift_plan plan, int32_t skew);
 
 /* Lanes of the plan's forward calls (1 or 2; default 2; the autotuner sets
- * it too; the affine-warped forward always uses one).  With 1 every launch goes to the call's stream and a
- * streaming slice holds up to min(max_windows, 2048) windows; with 2 the
- * slices hold up to half of that, alternating between the two lanes.  The
- * results do not depend on the lanes.  SWIFT_ERR_INVALID_ARG for other
- * values. */
+ * it too; the affine-warped forward always uses one).  With 1 every launch
+ * goes to the call's stream and a streaming slice holds up to
+ * S = min(max_windows, 2048) windows.  With 2 each level's windows are split
+ * into slices of about half the level (at least 256 windows, at most S, or
+ * S / 2 when S windows of the plan's largest size pass 2 GiB of workspace),
+ * each going to the less loaded lane; the workspace holds one such part per
+ * lane.  The results do not depend on the lanes.  SWIFT_ERR_INVALID_ARG for
+ * other values. */
 swift_status swift_plan_set_lanes(swift_plan plan, int32_t lanes);
 /* The plan's current lanes, into *lanes (host int32). */
 swift_status swift_plan_get_lanes(swift_plan plan, int32_t* lanes);

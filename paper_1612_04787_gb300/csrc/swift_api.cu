@@ -50,6 +50,7 @@ struct swift_plan_s {
   void* work = nullptr;
   long long work_windows = 0;  // windows per slice with one lane (of the largest streamed size)
   size_t work_per = 0;         // workspace bytes per window at the largest streamed size
+  long long lane_cap = 0;      // windows per streaming slice in each of two lanes (workspace part of each)
   unsigned int* done = nullptr;  // per-window block counters of the streaming finalize (kept zero)
   // lanes: the streams one forward call spreads its launch units over (the
   // call's stream and one auxiliary stream), each with its own part of the
@@ -110,6 +111,10 @@ constexpr int kSkews[] = {4, 8, 12, 16};
 // the lanes' workspace parts (256-aligned: the carve aligns within a part)
 constexpr int kMaxLanes = 2;
 long long lane_capacity(long long work_windows, int lanes) { return (work_windows + lanes - 1) / lanes; }
+// each lane's workspace part holds a full single-lane slice while that is at
+// most this many bytes, else half of one
+constexpr size_t kLaneBytes = size_t(2) << 30;
+constexpr long long kMinLaneSlice = 256;
 size_t lane_stride(size_t per, long long capacity) {
   return ((per * static_cast<size_t>(capacity) + 255) & ~static_cast<size_t>(255)) + 1024;
 }
@@ -255,9 +260,11 @@ extern "C" swift_status swift_plan_create(const swift_level* levels, int32_t n_l
   if (per > 0) {
     p->work_windows = max_windows < kStreamSlice ? max_windows : kStreamSlice;
     p->work_per = per;
-    // room for kMaxLanes lanes of lane_capacity windows each (at least the
-    // single-lane slice of work_windows)
-    const long long c = lane_capacity(p->work_windows, kMaxLanes);
+    // room for kMaxLanes lanes of lane_cap windows each (together at least
+    // the single-lane slice of work_windows)
+    p->lane_cap = per * static_cast<size_t>(p->work_windows) <= kLaneBytes ? p->work_windows
+                                                                         : lane_capacity(p->work_windows, kMaxLanes);
+    const long long c = p->lane_cap;
     const size_t bytes = kMaxLanes * lane_stride(per, c) + 4096;
     if (cudaMalloc(&p->work, bytes) != cudaSuccess ||
         cudaMalloc(&p->done, sizeof(unsigned int) * kMaxLanes * c) != cudaSuccess ||
@@ -359,6 +366,26 @@ static swift::MatchLaunch level_launch_forward(swift_plan plan, const swift_batc
   return L;
 }
 
+// Slices of a level's B streaming windows over the call's lanes: one lane
+// takes slices of the plan's full slice; two lanes split the level into
+// about equal slices (at least kMinLaneSlice, at most lane_cap windows), lane
+// k in its own part of the workspace and of the finalize counters.
+struct LaneSlices {
+  long long cap;       // windows per slice
+  size_t stride;       // bytes between the lanes' workspace parts
+  long long done_off;  // counters between the lanes' parts
+};
+static LaneSlices lane_slices(swift_plan plan, int lanes, long long B) {
+  if (lanes <= 1) return {plan->work_windows, 0, 0};
+  // a level is split only into slices of at least kMinLaneSlice windows (smaller
+  // levels take one slice each and alternate between the lanes)
+  long long cap = lane_capacity(B, lanes);
+  if (cap < kMinLaneSlice) cap = kMinLaneSlice;
+  if (cap > plan->lane_cap) cap = plan->lane_cap;
+  if (cap < 1) cap = 1;
+  return {cap, lane_stride(plan->work_per, plan->lane_cap), plan->lane_cap};
+}
+
 // Launch the windows of level l with the level's schedule (fused or
 // streaming) over the call's lanes: each streaming slice (at most the lane
 // capacity) and each fused launch goes to the least-loaded lane, a slice in
@@ -376,8 +403,9 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
   if (plan->prec != SWIFT_PREC_FP32) {
     // the tensor-core schedule's slices spread over the lanes like the FP32 ones
     const bool fp16 = plan->prec == SWIFT_PREC_FP16X2;
-    const long long cap = lane_capacity(plan->work_windows, ls.n);
-    const size_t stride = lane_stride(plan->work_per, cap);
+    const LaneSlices sl = lane_slices(plan, ls.n, B);
+    const long long cap = sl.cap;
+    const size_t stride = sl.stride;
     for (long long b0 = 0; b0 < B; b0 += cap) {
       const long long cnt = (B - b0) < cap ? (B - b0) : cap;
       const int k = lane_pick(ls, static_cast<double>(cnt) * lv.n * lv.n);
@@ -393,13 +421,14 @@ static swift_status run_level(swift_plan plan, const swift_batch* batch, int l, 
     return SWIFT_OK;
   }
   if (plan->sched[l] != SWIFT_SCHED_FUSED) {
-    const long long cap = lane_capacity(plan->work_windows, ls.n);
-    const size_t stride = lane_stride(plan->work_per, cap);
+    const LaneSlices sl = lane_slices(plan, ls.n, B);
+    const long long cap = sl.cap;
+    const size_t stride = sl.stride;
     for (long long b0 = 0; b0 < B; b0 += cap) {
       const long long cnt = (B - b0) < cap ? (B - b0) : cap;
       const int k = lane_pick(ls, static_cast<double>(cnt) * lv.n * lv.n);
       swift::StreamWork W = swift::stream_carve(static_cast<unsigned char*>(plan->work) + k * stride, cap, lv.n, b0, cnt);
-      W.done = plan->done + k * cap;
+      W.done = plan->done + k * sl.done_off;
       if (plan->timing) {
         const int set = plan->tcount++ % kTimingSets;
         // the launcher folds the finalize into the inverse rows for n <= 256 and radii below 8 px

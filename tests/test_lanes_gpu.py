@@ -54,11 +54,11 @@ def test_one_level_equals_one_lane(n, count):
 
 
 def test_several_slices_per_lane():
-    """max_windows above the 2048-window slice: with two lanes each lane takes
-    slices of 1024 windows, two of them here."""
+    """max_windows above the 2048-window slice: with two lanes the 5000
+    windows go out as slices of 2048, 2048 and 904, two of them on one lane."""
     a, b = synth.em_section_pair(1024, seed_content=211, seed_warp=212, seed_noise=(213, 214))
-    ro = synth.random_origins(4000, 1024, 1024, 128, seed=215)
-    plan = swift.Plan([swift.Level(128, 0.65)], dtype="u8", max_windows=4000)
+    ro = synth.random_origins(5000, 1024, 1024, 128, seed=215)
+    plan = swift.Plan([swift.Level(128, 0.65)], dtype="u8", max_windows=5000)
     one, two = _per_lanes(plan, T(a), T(b), T(ro), T(ro))
     assert torch.equal(one, two)
     assert (swift.decode(two)["status"] == 0).all()
