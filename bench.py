@@ -303,7 +303,8 @@ class Sections:
     name = "sections"
     dominant_n = 256
 
-    def __init__(self, torch, swift, dev, pairs=1, windows=0, precision="fp32", rank=0, lanes=0):
+    def __init__(self, torch, swift, dev, pairs=1, windows=0, precision="fp32", rank=0, lanes=0, mov_shift=0,
+                 row_tma=-1):
         import synth
         self.n, self.w, self.r, self.size, self.stride = 256, 0.65, 3.0, 4096, 128
         # the job is world x pairs section pairs: rank r matches pairs r*pairs .. r*pairs + pairs - 1
@@ -313,37 +314,54 @@ class Sections:
                                            seed_noise=(2 + 10 * p, 3 + 10 * p)) for p in range(first, first + pairs)]
         org = synth.grid_origins(self.size, self.n, self.stride)
         self.org = org[:windows] if windows > 0 else org
+        # moving windows mov_shift px right of the reference windows (left where
+        # that would leave the section): rows off 16-byte boundaries
+        self.morg = self.org.copy()
+        if mov_shift:
+            x = self.morg[:, 1]
+            self.morg[:, 1] = np.where(x + mov_shift <= self.size - self.n, x + mov_shift, x - mov_shift)
         g = (self.size - self.n) // self.stride + 1
         self.description = (f"{g}x{g} grid of {self.n}x{self.n} windows (stride {self.stride}) on a "
                             f"{self.size}x{self.size} uint8 EM-like section pair")
+        if mov_shift:
+            self.description += f", moving windows shifted {mov_shift} px in x"
         self.B1 = len(self.org)
         self.windows = self.B1 * pairs
         self.plan = swift.Plan([swift.Level(self.n, self.w, "hann", 1.0, self.r)], dtype="u8",
                                precision=precision, max_windows=self.B1)
         if lanes:
             self.plan.set_lanes(lanes)
+        if row_tma >= 0:
+            self.plan.set_row_tma(row_tma)
         self.d = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in self.secs]
         self.dorg = torch.from_numpy(self.org).to(dev)
+        self.shifted = mov_shift != 0  # else the moving windows use the reference origins' buffers
+        self.dmorg = torch.from_numpy(self.morg).to(dev) if self.shifted else self.dorg
         self.outs = [torch.empty((self.B1, 8), dtype=torch.int32, device=dev) for _ in self.secs]
         self.h = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in self.secs]
         self.horg = torch.from_numpy(self.org).pin_memory()
+        self.hmorg = torch.from_numpy(self.morg).pin_memory() if self.shifted else self.horg
         self.hout = [torch.empty((self.B1, 8), dtype=torch.int32).pin_memory() for _ in self.secs]
         self.flops = flops_per_pair(self.n) * self.windows
         self.launches_per_step = 3 * self.plan.lanes * len(self.secs)
         self.config = {"window": self.n, "windows_per_step": self.windows, "section_pairs_per_step": pairs,
                        "whiten_exponent": self.w, "apod": "hann", "snr_exclusion_radius": self.r, "input": "uint8",
-                       "lanes": self.plan.lanes}
+                       "lanes": self.plan.lanes, "row_tma": self.plan.row_tma}
+        if mov_shift:
+            self.config["mov_shift_x"] = mov_shift
 
     def step(self, stream):
         for (a, b), o in zip(self.d, self.outs):
-            self.plan.match(a, b, self.dorg, self.dorg, out=o, stream=stream)
+            self.plan.match(a, b, self.dorg, self.dmorg, out=o, stream=stream)
 
     def e2e_step(self, torch, stream):
         self.dorg.copy_(self.horg, non_blocking=True)
+        if self.shifted:
+            self.dmorg.copy_(self.hmorg, non_blocking=True)
         for (ha, hb), (da, db), o, ho in zip(self.h, self.d, self.outs, self.hout):
             da.copy_(ha, non_blocking=True)
             db.copy_(hb, non_blocking=True)
-            self.plan.match(da, db, self.dorg, self.dorg, out=o, stream=stream)
+            self.plan.match(da, db, self.dorg, self.dmorg, out=o, stream=stream)
             ho.copy_(o, non_blocking=True)
         stream.synchronize()
 
@@ -355,33 +373,36 @@ class Sections:
         if not hasattr(self, "d2"):
             self.d2 = [(torch.empty_like(a), torch.empty_like(b)) for a, b in self.d]
             self.org2 = torch.empty_like(self.dorg)
+            self.morg2 = torch.empty_like(self.dmorg) if self.shifted else self.org2
             self.outs2 = [torch.empty_like(o) for o in self.outs]
             self.copy_stream = torch.cuda.Stream(device=self.dorg.device)
-        sets = [(self.d, self.dorg, self.outs), (self.d2, self.org2, self.outs2)]
+        sets = [(self.d, self.dorg, self.dmorg, self.outs), (self.d2, self.org2, self.morg2, self.outs2)]
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         done = [torch.cuda.Event(), torch.cuda.Event()]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(steps):
-            d, org, outs = sets[k % 2]
+            d, org, morg, outs = sets[k % 2]
             if k >= 2:
                 self.copy_stream.wait_event(done[k % 2])  # step k - 2 no longer reads these buffers
             with torch.cuda.stream(self.copy_stream):
                 org.copy_(self.horg, non_blocking=True)
+                if self.shifted:
+                    morg.copy_(self.hmorg, non_blocking=True)
                 for (ha, hb), (da, db) in zip(self.h, d):
                     da.copy_(ha, non_blocking=True)
                     db.copy_(hb, non_blocking=True)
                 copied[k % 2].record(self.copy_stream)
             stream.wait_event(copied[k % 2])
             for (da, db), o, ho in zip(d, outs, self.hout):
-                self.plan.match(da, db, org, org, out=o, stream=stream)
+                self.plan.match(da, db, org, morg, out=o, stream=stream)
                 ho.copy_(o, non_blocking=True)
             done[k % 2].record(stream)
         stream.synchronize()
         return time.perf_counter() - t0
 
     def io_bytes(self):
-        return sum(a.nbytes + b.nbytes for a, b in self.secs) + self.org.nbytes, self.windows * 32
+        return sum(a.nbytes + b.nbytes for a, b in self.secs) + self.org.nbytes * (2 if self.shifted else 1), self.windows * 32
 
     def ok_fraction(self, swift):
         return float((swift.decode(self.outs[0])["status"] == 0).mean())
@@ -398,10 +419,9 @@ class Sections:
 
     def oracle_windows(self, k):
         a, b = self.secs[0]
-        o = self.org[:k]
         n = self.n
-        return ([b[y:y + n, x:x + n].astype(np.float64) for y, x in o],
-                [a[y:y + n, x:x + n].astype(np.float64) for y, x in o], n, self.w, self.r)
+        return ([b[y:y + n, x:x + n].astype(np.float64) for y, x in self.morg[:k]],
+                [a[y:y + n, x:x + n].astype(np.float64) for y, x in self.org[:k]], n, self.w, self.r)
 
 
 class Noise64:
@@ -754,7 +774,8 @@ class Whitening:
 def make_workload(name, torch, swift, dev, args):
     if name == "sections":
         return Sections(torch, swift, dev, pairs=args.pairs, windows=args.windows, precision=args.precision,
-                        rank=int(os.environ.get("RANK", "0")), lanes=args.lanes)
+                        rank=int(os.environ.get("RANK", "0")), lanes=args.lanes, mov_shift=args.mov_shift,
+                        row_tma=args.row_tma)
     if name == "noise64":
         return Noise64(torch, swift, dev)
     if name == "pyramid":
@@ -1175,6 +1196,11 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2],
                     help="streams an FP32 call spreads over (0: the plan's default / the autotuner's pick)")
     ap.add_argument("--windows", type=int, default=0, help="limit the windows per step (small profiling cases)")
+    ap.add_argument("--mov-shift", type=int, default=0,
+                    help="sections: moving windows shifted this many px in x (rows off 16-byte boundaries)")
+    ap.add_argument("--row-tma", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="sections: uint8 row loads (0 plain, 1 tile copies for unaligned rows, 2 tile copies; "
+                         "-1 the plan's default)")
     ap.add_argument("--oracle-sample", type=int, default=961)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the cuFFT and host-FFT comparisons")

@@ -332,6 +332,22 @@ swift_status swift_plan_set_lanes(swift_plan plan, int32_t lanes);
 /* The plan's current lanes, into *lanes (host int32). */
 swift_status swift_plan_get_lanes(swift_plan plan, int32_t* lanes);
 
+/* How the streaming row kernel loads uint8 section windows (Sec. II: the
+ * windows cut from the two images): 0 by plain loads only (16-byte vectors
+ * where a window's rows start on a 16-byte boundary, else byte loads); 1 (the
+ * default) through tensor-map (TMA) tile copies for the windows whose rows
+ * start off a 16-byte boundary in either image, plain vectors for the rest;
+ * 2 through tensor-map copies for every window.  A tile copy takes the rows
+ * of one row block from the 16-byte chunk holding the window's first column
+ * (so the copy starts aligned whatever the origin) into shared memory, and
+ * the kernel reads the window from the origin's offset in the chunk.  Tile
+ * copies need 16-byte aligned image addresses, pitches and widths and a
+ * one-section reference; other images load as with 0.  The results do not
+ * depend on the mode.  SWIFT_ERR_INVALID_ARG for other values. */
+swift_status swift_plan_set_row_tma(swift_plan plan, int32_t mode);
+/* The plan's current mode, into *mode (host int32). */
+swift_status swift_plan_get_row_tma(swift_plan plan, int32_t* mode);
+
 /* Capture one forward call on `batch` (all its levels) into a CUDA graph
  * owned by the plan; swift_plan_replay then re-runs it with one graph
  * launch.  Pointers and sizes are baked into the graph: replay matches the
@@ -357,14 +373,15 @@ swift_status swift_plan_replay(swift_plan plan, void* stream);
 swift_status swift_plan_set_timing(swift_plan plan, int32_t enable);
 
 /* Test hook for the bounded-wait failure path (not for production use).
- * While enabled, the FP32 streaming schedule's staging of aligned float32
- * rows (bulk asynchronous copies counted on an mbarrier) expects 16 bytes
- * more than its copies deliver, so its wait gives up after its bound (about
- * 2 s, then about 2 s more for copies in flight) and every such window
+ * While enabled, the FP32 streaming schedule's row staging by asynchronous
+ * copies counted on an mbarrier (bulk copies of aligned float32 rows, and the
+ * tensor-map tile copies of uint8 rows, swift_plan_set_row_tma) expects 16
+ * bytes more than its copies deliver, so its wait gives up after its bound
+ * (about 2 s, then about 2 s more for copies in flight) and every such window
  * reports SWIFT_WIN_TIMEOUT.  Nothing faults or hangs; the stream and the
  * plan stay usable, and calls after disabling it give normal results.
- * uint8 windows, the fused schedule and the tensor-core forms do not use
- * this staging and are unaffected. */
+ * Windows loaded by plain loads, the fused schedule and the tensor-core forms
+ * do not use this staging and are unaffected. */
 swift_status swift_plan_set_test_stall(swift_plan plan, int32_t enable);
 
 /* Test hook for the persistent schedule's bounded waits (not for production

@@ -187,8 +187,9 @@ class Plan:
     KERNEL_SLOTS = ("stats", "rows", "cols", "irows", "final", "fused", "persistent")
 
     def set_test_stall(self, enable: bool):
-        """Test hook: float32 row staging waits for bytes that never arrive,
-        so its bounded wait runs out and windows report status 4 (timeout)."""
+        """Test hook: the row staging by asynchronous copies (aligned float32
+        rows, uint8 tensor-map tiles) waits for bytes that never arrive, so its
+        bounded wait runs out and those windows report status 4 (timeout)."""
         check(lib.swift_plan_set_test_stall(self._h, 1 if enable else 0), "swift_plan_set_test_stall")
 
     def set_skew(self, skew: int):
@@ -204,6 +205,18 @@ class Plan:
     def lanes(self) -> int:
         v = C.c_int32(0)
         check(lib.swift_plan_get_lanes(self._h, C.byref(v)), "swift_plan_get_lanes")
+        return int(v.value)
+
+    def set_row_tma(self, mode: int):
+        """How the streaming row kernel loads uint8 section windows: 0 plain
+        loads only, 1 (default) tensor-map tile copies for windows whose rows
+        start off a 16-byte boundary, 2 tensor-map copies for every window."""
+        check(lib.swift_plan_set_row_tma(self._h, int(mode)), "swift_plan_set_row_tma")
+
+    @property
+    def row_tma(self) -> int:
+        v = C.c_int32(0)
+        check(lib.swift_plan_get_row_tma(self._h, C.byref(v)), "swift_plan_get_row_tma")
         return int(v.value)
 
     def set_test_hold(self, window: int):

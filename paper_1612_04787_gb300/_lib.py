@@ -45,6 +45,8 @@ EXPORTS = (
     "swift_plan_set_skew",
     "swift_plan_set_lanes",
     "swift_plan_get_lanes",
+    "swift_plan_set_row_tma",
+    "swift_plan_get_row_tma",
     "swift_plan_set_test_stale_status",
     "swift_window_check",
     "swift_plan_timings",
@@ -135,6 +137,10 @@ def _load():
     lib.swift_plan_set_lanes.restype = C.c_int
     lib.swift_plan_get_lanes.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     lib.swift_plan_get_lanes.restype = C.c_int
+    lib.swift_plan_set_row_tma.argtypes = [C.c_void_p, C.c_int32]
+    lib.swift_plan_set_row_tma.restype = C.c_int
+    lib.swift_plan_get_row_tma.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    lib.swift_plan_get_row_tma.restype = C.c_int
     lib.swift_plan_set_test_stale_status.argtypes = [C.c_void_p, C.c_int32]
     lib.swift_plan_set_test_stale_status.restype = C.c_int
     lib.swift_window_check.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32),

@@ -56,6 +56,7 @@ struct swift_plan_s {
   // call's stream and one auxiliary stream), each with its own part of the
   // workspace; fork / join events order the auxiliary lane with the call
   int lanes = 2;
+  int row_tma = 1;  // swift_plan_set_row_tma
   cudaStream_t aux = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // affine-warp forward and backward: allocated on first use
@@ -346,6 +347,7 @@ static swift::MatchLaunch level_launch_forward(swift_plan plan, const swift_batc
   L.twiddle = plan->twiddle[size_slot(lv.n)];
   L.stall_tx = plan->test_stall ? 16u : 0u;
   L.stale_ok = plan->test_stale_ok ? 1 : 0;
+  L.row_tma = plan->row_tma;
   L.out = out;
   if (batch->level_offsets) {
     // a batch sorted by level: this level's windows only, as a batch of their own
@@ -952,6 +954,18 @@ extern "C" swift_status swift_plan_set_lanes(swift_plan plan, int32_t lanes) {
 extern "C" swift_status swift_plan_get_lanes(swift_plan plan, int32_t* lanes) {
   if (!plan || !lanes) return SWIFT_ERR_INVALID_ARG;
   *lanes = plan->aux ? plan->lanes : 1;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_set_row_tma(swift_plan plan, int32_t mode) {
+  if (!plan || mode < 0 || mode > 2) return SWIFT_ERR_INVALID_ARG;
+  plan->row_tma = mode;
+  return SWIFT_OK;
+}
+
+extern "C" swift_status swift_plan_get_row_tma(swift_plan plan, int32_t* mode) {
+  if (!plan || !mode) return SWIFT_ERR_INVALID_ARG;
+  *mode = plan->row_tma;
   return SWIFT_OK;
 }
 

@@ -1,5 +1,6 @@
 // Internal launch descriptors shared by the host API and the kernels.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the structure; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -75,8 +76,24 @@ struct MatchLaunch {
   const float* ahat = nullptr;       // [n] DFT of the 1D taper (real: the taper is symmetric), or null
   swift_result* out;                 // [B]
   const int* pre_status = nullptr;   // [slice] status decided before the statistics (or null)
-  unsigned int stall_tx = 0;         // test hook: bytes the float row staging waits for that never arrive
+  unsigned int stall_tx = 0;         // test hook: bytes the row staging copies wait for that never arrive
+  int row_tma = 1;                   // uint8 section rows through tensor maps: 0 never, 1 windows whose
+                                     // rows start off a 16-byte boundary, 2 every window (RowMaps)
   int stale_ok = 0;                  // test hook: statistics report OK for windows of other levels
+};
+
+// Tensor maps of the row kernel's uint8 window tiles, one per section image:
+// the image seen as [height][width / 16][16] bytes (row stride the pitch),
+// box [RB][n / 16 + 1][16], i.e. the RB rows of a row block from the 16-byte
+// chunk that holds the window's first column through the chunk after its
+// last, into shared memory rows of n + 16 bytes.  The copy's innermost
+// coordinate is always 0 (16-byte aligned whatever the origin); the kernel
+// reads the window from byte x mod 16 of each row.  Needs 16-byte aligned
+// data, pitch and width (else `on` stays 0 and the rows load without them).
+struct RowMaps {
+  CUtensorMap mov, ref;
+  int on;   // 1: both maps hold
+  int all;  // 1: every window loads through the maps; 0: only windows whose rows start off a 16-byte boundary
 };
 
 // Workspace of the streaming forward path for one slice of windows.

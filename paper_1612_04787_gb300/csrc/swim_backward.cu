@@ -72,7 +72,7 @@ cudaError_t backward_n(const MatchLaunch& L, const BackLaunch& K, const BackWork
   W.b0 = 0;
   // forward recompute, keeping C and R
   stream_stats_kernel<N, float><<<S, 256, 0, st>>>(P, W);
-  stream_rows_kernel<N, float><<<S * (N / G::RB), 256, rows_smem<N, float>(), st>>>(P, W);
+  stream_rows_kernel<N, float><<<S * (N / G::RB), 256, rows_smem<N, float>(), st>>>(P, W, RowMaps{});
   stream_cols_kernel<N, true><<<S * G::NB2, G::T2, cols_smem<N>(), st>>>(P, W, BW.cr);
   stream_irows_kernel<N><<<S * G::NB3, 256, irows_smem<N>(), st>>>(P, W);
   back_stats_kernel<N><<<S, 32, 0, st>>>(P, W, BW.bst);

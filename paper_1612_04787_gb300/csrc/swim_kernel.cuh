@@ -216,6 +216,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(mbar)
       : "memory");
 }
+// Tiled tensor copy of the box at (c0, c1, c2) of a 3D tensor map (the map a
+// __grid_constant__ kernel argument) into shared memory at `dst` (128-byte
+// aligned), its bytes counted on the mbarrier; boxes reaching past the
+// tensor's extent read zeros there.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int c0, int c1, int c2, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+      : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // reductions

@@ -7,6 +7,59 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// cuTensorMapEncodeTiled from the driver, fetched once through the runtime
+// (the library links no driver library); null when the driver has none
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static const EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// The tile map of one uint8 section image (RowMaps): [h][w / 16][16] bytes,
+// box [rb][n / 16 + 1][16]; false where the image's address, pitch or width
+// is not a multiple of 16 bytes or the driver refuses the map.
+bool tile_map(CUtensorMap* m, const void* data, int h, int w, long long pitch, int n, int rb) {
+  const EncodeTiled enc = encode_tiled();
+  if (!enc || !data || h < 1 || w < 16 || (reinterpret_cast<uintptr_t>(data) & 15) || (pitch & 15) || (w & 15) ||
+      pitch < w)
+    return false;
+  const cuuint64_t dim[3] = {16, static_cast<cuuint64_t>(w / 16), static_cast<cuuint64_t>(h)};
+  const cuuint64_t stride[2] = {16, static_cast<cuuint64_t>(pitch)};
+  const cuuint32_t box[3] = {16, static_cast<cuuint32_t>(n / 16 + 1), static_cast<cuuint32_t>(rb)};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(data), dim, stride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The row kernel's tensor maps for a launch: uint8 section windows with a
+// one-section reference, when MatchLaunch::row_tma asks for them
+template <int N, typename TIn>
+RowMaps row_maps(const MatchLaunch& L) {
+  RowMaps M{};
+  if constexpr (sizeof(TIn) == 1) {
+    if (L.row_tma == 0 || L.patch_mode || L.ref_count != 1) return M;
+    constexpr int RB = StreamGeom<N>::RB;
+    if (!tile_map(&M.mov, L.mov, L.mov_h, L.mov_w, L.mov_pitch, N, RB) ||
+        !tile_map(&M.ref, L.ref, L.ref_h, L.ref_w, L.ref_pitch, N, RB))
+      return RowMaps{};
+    M.on = 1;
+    M.all = L.row_tma == 2 ? 1 : 0;
+  }
+  return M;
+}
+
 template <int N>
 size_t part_blocks() {
   return StreamGeom<N>::NB3;
@@ -55,17 +108,18 @@ cudaError_t launch_n(const MatchLaunch& L, const StreamWork& W, cudaStream_t st)
   auto mark = [&](int k) {
     if (W.ev) cudaEventRecord(W.ev[k], st);
   };
+  const RowMaps M = row_maps<N, TIn>(L);
   mark(0);
   if (!fold_stats) stream_stats_kernel<N, TIn><<<S, 256, 0, st>>>(L, W);
   mark(1);
   if constexpr (kPair) {
     if (fold_stats) {
-      stream_rows_kernel<N, TIn, true><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+      stream_rows_kernel<N, TIn, true><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W, M);
     } else {
-      stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+      stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W, M);
     }
   } else {
-    stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W);
+    stream_rows_kernel<N, TIn><<<S * (N / G::RB), 256, rows_smem<N, TIn>(), st>>>(L, W, M);
   }
   mark(2);
   if constexpr (kPair) {

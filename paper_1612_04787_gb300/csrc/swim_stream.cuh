@@ -342,6 +342,28 @@ __device__ __forceinline__ void transpose16_u8(uint32_t (&w)[4], int L) {
   }
 }
 
+// Bytes 16 c + o .. 16 c + o + 15 (0 <= o < 16) of a shared-memory row that
+// starts on a 16-byte boundary, as four little-endian words: two 16-byte
+// loads (one when o = 0, which the window makes uniform over the CTA) and a
+// funnel shift by o bytes.  The row holds at least 16 (c + 2) bytes.
+__device__ __forceinline__ void tile_bytes16(const unsigned char* row, int c, int o, uint32_t (&w)[4]) {
+  const uint4* p = reinterpret_cast<const uint4*>(row) + c;
+  const uint4 a = p[0];
+  if (o == 0) {
+    w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
+    return;
+  }
+  const uint4 n = p[1];
+  const uint32_t u[8] = {a.x, a.y, a.z, a.w, n.x, n.y, n.z, n.w};
+  const int k = o >> 2;
+  const uint32_t sh = 8u * static_cast<uint32_t>(o & 3);
+  uint32_t d[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) d[i] = k == 0 ? u[i] : (k == 1 ? u[i + 1] : (k == 2 ? u[i + 2] : u[i + 3]));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = __funnelshift_r(d[q], d[q + 1], sh);
+}
+
 // per-warp partials of a row block's statistics (STATS mode), in shared memory
 struct RowBlockSums {
   float s[8][2];
@@ -361,7 +383,7 @@ __device__ __forceinline__ RowBlockSums& row_block_sums() {
 // pixel (so a window is flat when no block sets the bit), bit 2 a non-finite
 // float pixel.  The column-pair kernel removes the means in the spectrum.
 template <int N, typename TIn, bool STATS = false>
-__device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R, int rb) {
+__device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R, int rb, const RowMaps* M = nullptr) {
   using G = StreamGeom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, RB = G::RB, RS = G::RS, T = G::T;
   constexpr int KB = (RB * R1 + T - 1) / T;
@@ -398,27 +420,69 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
   TIn* mstage = reinterpret_cast<TIn*>(tapT + R2 * TS);  // [RB][MS]
   TIn* rstage = mstage + RB * MS;
   float* rfstage = reinterpret_cast<float*>(slab);
+  const TIn* mbase;
+  const TIn* rbase;
+  long long mpitch, rpitch;
+  int my = 0, mx = 0, ry = 0, rx = 0;
+  if (L.patch_mode) {
+    mbase = static_cast<const TIn*>(L.mov) + b * L.mov_stride;
+    rbase = static_cast<const TIn*>(L.ref) + b * L.ref_stride;
+    mpitch = rpitch = N;
+  } else {
+    my = __ldg(L.mov_origin + 2 * b);
+    mx = __ldg(L.mov_origin + 2 * b + 1);
+    ry = __ldg(L.ref_origin + 2 * b);
+    rx = __ldg(L.ref_origin + 2 * b + 1);
+    mbase = static_cast<const TIn*>(L.mov) + static_cast<long long>(my) * L.mov_pitch + mx;
+    rbase = static_cast<const TIn*>(L.ref) + static_cast<long long>(ry) * L.ref_pitch + rx;
+    mpitch = L.mov_pitch;
+    rpitch = L.ref_pitch;
+  }
+  // uint8 section rows through the tensor maps (RowMaps): the tiles start at
+  // the staging area's first 128-byte boundary (rows_smem leaves the slack);
+  // one thread issues both box copies before the tables are staged, so the
+  // copies run under the table loads
+  __shared__ __align__(8) unsigned long long stage_bar;
+  const uint32_t mbar = smem_addr(&stage_bar);
+  bool tma = false;
+  TIn* mtile = mstage;
+  if constexpr (sizeof(TIn) == 1) {
+    tma = M != nullptr && M->on && (M->all || ((mx | rx) & 15) != 0);
+    const uint32_t a = smem_addr(mstage);
+    mtile = mstage + (((a + 127u) & ~127u) - a);
+  }
+  TIn* rtile = mtile + RB * MS;
+  if constexpr (sizeof(TIn) == 1) {
+    static_assert(MS == N + 16, "tile rows of n / 16 + 1 chunks of 16 bytes");
+    if (tma && tid == 0) {
+      mbar_init(mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(mbar, 2 * RB * MS + L.stall_tx);
+      tma_load_3d(smem_addr(mtile), &M->mov, 0, mx >> 4, my + rb * RB, mbar);
+      tma_load_3d(smem_addr(rtile), &M->ref, 0, rx >> 4, ry + rb * RB, mbar);
+    }
+  }
   for (int i = tid; i < N; i += T) {
     twid[i] = L.twiddle[i];
     const float t = L.taper[i];
     tap[i] = t;
     tapT[(i % R2) * TS + i / R2] = t;
   }
-  const TIn* mbase;
-  const TIn* rbase;
-  long long mpitch, rpitch;
-  if (L.patch_mode) {
-    mbase = static_cast<const TIn*>(L.mov) + b * L.mov_stride;
-    rbase = static_cast<const TIn*>(L.ref) + b * L.ref_stride;
-    mpitch = rpitch = N;
-  } else {
-    mbase = static_cast<const TIn*>(L.mov) + static_cast<long long>(__ldg(L.mov_origin + 2 * b)) * L.mov_pitch +
-            __ldg(L.mov_origin + 2 * b + 1);
-    rbase = static_cast<const TIn*>(L.ref) + static_cast<long long>(__ldg(L.ref_origin + 2 * b)) * L.ref_pitch +
-            __ldg(L.ref_origin + 2 * b + 1);
-    mpitch = L.mov_pitch;
-    rpitch = L.ref_pitch;
-  }
+  // a staging copy that did not arrive (bounded wait): the window is marked
+  // SWIFT_WIN_TIMEOUT after one more wait for the copies in flight
+  auto staging_timeout = [&]() {
+    if (tid == 0) {
+      mbar_wait_bounded(mbar, 0);
+      *R.stats = make_float4(0.f, 0.f, __int_as_float(SWIFT_WIN_TIMEOUT), 0.f);
+      if constexpr (STATS) {
+        // block 0 may write OK after this: the record carries the timeout
+        float* rec = R.rstat + 8 * rb;
+        rec[0] = rec[1] = rec[2] = rec[3] = 0.f;
+        rec[4] = __int_as_float(kRowTimeout);
+      }
+    }
+  };
   // STATS: the windows' first pixels (the reference's as the staged rows
   // average a K-section model), which the block's pixels are compared with
   float p0m = 0.f, p0r = 0.f;
@@ -444,7 +508,19 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
                                          static_cast<uintptr_t>(mpitch * sizeof(TIn)) |
                                          static_cast<uintptr_t>(rpitch * sizeof(TIn))) & 15) == 0;
   uint32_t wm[4] = {0u, 0u, 0u, 0u}, wr[4] = {0u, 0u, 0u, 0u};  // kShfl: bytes 16 L .. 16 L + 15 of a row
-  if (vec) {
+  if (tma) {
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    const bool arrived = mbar_wait_bounded(mbar, 0);
+    if (__syncthreads_or(!arrived)) {
+      staging_timeout();
+      return;
+    }
+    if constexpr (kShfl) {
+      const int r = tid / 16, c = tid % 16;
+      tile_bytes16(mtile + r * MS, c, mx & 15, wm);
+      tile_bytes16(rtile + r * MS, c, rx & 15, wr);
+    }
+  } else if (vec) {
     if constexpr (kShfl) {
       static_assert(RB * N / 16 == T && R2 == 16, "one 16-byte vector per thread and window");
       const int r = tid / 16, x0 = (tid % 16) * 16;
@@ -453,8 +529,6 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
       wm[0] = a.x, wm[1] = a.y, wm[2] = a.z, wm[3] = a.w;
       wr[0] = c.x, wr[1] = c.y, wr[2] = c.z, wr[3] = c.w;
     } else if constexpr (sizeof(TIn) == 4) {
-      __shared__ __align__(8) unsigned long long stage_bar;
-      const uint32_t mbar = smem_addr(&stage_bar);
       constexpr uint32_t kRowBytes = N * sizeof(TIn);
       static_assert(kRowBytes % 16 == 0 && (MS * sizeof(TIn)) % 16 == 0, "bulk copy granularity");
       if (tid == 0) {
@@ -470,16 +544,7 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
       __syncthreads();  // the barrier is initialised before anyone waits on it
       const bool arrived = mbar_wait_bounded(mbar, 0);
       if (__syncthreads_or(!arrived)) {
-        if (tid == 0) {
-          mbar_wait_bounded(mbar, 0);
-          *R.stats = make_float4(0.f, 0.f, __int_as_float(SWIFT_WIN_TIMEOUT), 0.f);
-          if constexpr (STATS) {
-            // block 0 may write OK after this: the record carries the timeout
-            float* rec = R.rstat + 8 * rb;
-            rec[0] = rec[1] = rec[2] = rec[3] = 0.f;
-            rec[4] = __int_as_float(kRowTimeout);
-          }
-        }
+        staging_timeout();
         return;
       }
     } else {
@@ -518,14 +583,24 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
       rfstage[r * MS + x] = rv;
     }
   }
-  __syncthreads();
+  if (!tma) __syncthreads();  // (the tensor-map tiles: each thread saw the copies arrive)
+  // the rows as uint8 / float32 values: in registers (kShfl), else staged
+  const bool regs = vec || tma;
+  const TIn* ms = mstage;
+  const TIn* rs = rstage;
+  if constexpr (sizeof(TIn) == 1) {
+    if (tma) {
+      ms = mtile + (mx & 15);
+      rs = rtile + (rx & 15);
+    }
+  }
   // pass A: thread (line, j) takes x = j + R2 m of row rb*RB + line
   const int line = tid / R2, j = tid % R2;
   const int y = rb * RB + line;
   float mv[R1], rv[R1];
   int rflags = 0;  // STATS: this thread's record flags
   if constexpr (STATS && kShfl) {
-    if (vec) {
+    if (regs) {
       // the thread's 16 bytes of each row against the first pixel replicated
       const uint32_t rm = 0x01010101u * static_cast<uint32_t>(p0m), rr = 0x01010101u * static_cast<uint32_t>(p0r);
       uint32_t dm = 0u, dr = 0u;
@@ -537,7 +612,7 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
       rflags = (dm ? kRowDiffM : 0) | (dr ? kRowDiffR : 0);
     }
   }
-  if (kShfl && vec) {
+  if (kShfl && regs) {
     // lane j of the half-warp of row `line` receives x = j + 16 m, m = 0..15
     transpose16_u8(wm, j);
     transpose16_u8(wr, j);
@@ -550,12 +625,12 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
 #pragma unroll
     for (int m = 0; m < R1; ++m) {
       const int e = line * MS + j + R2 * m;
-      mv[m] = static_cast<float>(mstage[e]);
-      rv[m] = vec ? static_cast<float>(rstage[e]) : rfstage[e];
+      mv[m] = static_cast<float>(ms[e]);
+      rv[m] = regs ? static_cast<float>(rs[e]) : rfstage[e];
     }
   }
   if constexpr (STATS) {
-    if (!(kShfl && vec)) {
+    if (!(kShfl && regs)) {
 #pragma unroll
       for (int m = 0; m < R1; ++m) {
         rflags |= (mv[m] != p0m ? kRowDiffM : 0) | (rv[m] != p0r ? kRowDiffR : 0);
@@ -565,7 +640,7 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
       }
     }
   }
-  if (!vec) __syncthreads();  // rfstage aliases the slab written below
+  if (!regs) __syncthreads();  // rfstage aliases the slab written below
   {
     const float ay = tap[y];
     float tx[R1];
@@ -648,9 +723,10 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
 }
 
 template <int N, typename TIn, bool STATS = false>
-__global__ void __launch_bounds__(256, N == 512 ? 1 : 4) stream_rows_kernel(const MatchLaunch L, const StreamWork W) {
+__global__ void __launch_bounds__(256, N == 512 ? 1 : 4)
+    stream_rows_kernel(const MatchLaunch L, const StreamWork W, const __grid_constant__ RowMaps M) {
   constexpr int NRB = N / StreamGeom<N>::RB;
-  rows_stage<N, TIn, STATS>(L, slice_ref<N>(L, W, blockIdx.x / NRB), blockIdx.x % NRB);
+  rows_stage<N, TIn, STATS>(L, slice_ref<N>(L, W, blockIdx.x / NRB), blockIdx.x % NRB, &M);
 }
 
 // ---------------------------------------------------------------------------
@@ -1604,8 +1680,9 @@ __global__ void __launch_bounds__(128, 5) stream_peak_kernel(const MatchLaunch L
 template <int N, typename TIn>
 constexpr size_t rows_smem() {
   using G = StreamGeom<N>;
+  // (uint8: 128 bytes of slack that align the tensor-map tiles)
   return sizeof(float2) * (G::RB * G::RS + N) + sizeof(float) * (N + G::R2 * (G::R1 + 4)) +
-         2 * sizeof(TIn) * G::RB * G::template stage_stride<TIn>();
+         2 * sizeof(TIn) * G::RB * G::template stage_stride<TIn>() + (sizeof(TIn) == 1 ? 128 : 0);
 }
 template <int N>
 constexpr size_t cols_smem() {
