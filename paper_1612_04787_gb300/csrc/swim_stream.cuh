@@ -1281,7 +1281,7 @@ __device__ __forceinline__ void irows_stage(const MatchLaunch& L, const WinRef& 
   float2* slab = reinterpret_cast<float2*>(smem_raw);  // [PB][RS]
   float2* twid = slab + PB * RS;
   __shared__ unsigned long long wkey[T / 32];
-  __shared__ double wsum[T / 32][2];
+  __shared__ float4 wsum[T / 32];  // per warp: the float pairs (hi, lo) of the sums of s and s^2
   for (int i = tid; i < N; i += T) twid[i] = L.twiddle[i];
   const float2* hw = R.h;
   irow_assemble<N, PB, T>(hw, slab, PB, [&](int p) { return pb * PB + p; }, tid);
@@ -1330,18 +1330,25 @@ __device__ __forceinline__ void irows_stage(const MatchLaunch& L, const WinRef& 
     best = ka > kb ? ka : kb;
   }
   best = warp_max_u64(best);
-  const double d1 = warp_sum_ff(s1), d2 = warp_sum_ff(s2);
+  // the block's sums as float pairs (FP32 additions with their errors kept),
+  // over the lanes and then over the warps; one FP64 addition per total
+  float h1 = s1, l1 = 0.f, h2 = s2, l2 = 0.f;
+  warp_sum_ff2(h1, l1);
+  warp_sum_ff2(h2, l2);
   if (lane == 0) {
     wkey[warp] = best;
-    wsum[warp][0] = d1;
-    wsum[warp][1] = d2;
+    wsum[warp] = make_float4(h1, l1, h2, l2);
   }
   __syncthreads();
   if (warp == 0) {
     const unsigned long long k = warp_max_u64(lane < T / 32 ? wkey[lane] : 0ull);
-    const double t1 = warp_sum_f64(lane < T / 32 ? wsum[lane][0] : 0.0);
-    const double t2 = warp_sum_f64(lane < T / 32 ? wsum[lane][1] : 0.0);
+    const float4 q = lane < T / 32 ? wsum[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float a1 = q.x, e1 = q.y, a2 = q.z, e2 = q.w;
+    warp_sum_ff2(a1, e1);
+    warp_sum_ff2(a2, e2);
     if (lane == 0) {
+      const double t1 = static_cast<double>(a1) + static_cast<double>(e1);
+      const double t2 = static_cast<double>(a2) + static_cast<double>(e2);
       unsigned long long* part = R.part + 3 * pb;
       part[0] = k;
       part[1] = static_cast<unsigned long long>(__double_as_longlong(t1));
@@ -1351,7 +1358,8 @@ __device__ __forceinline__ void irows_stage(const MatchLaunch& L, const WinRef& 
   if constexpr (kFold) {
     if (R.done != nullptr) {
       __shared__ int s_last;
-      __syncthreads();  // this block's partial is written
+      // (thread 0 wrote this block's partial itself: its fence below orders
+      // the partial before its ticket)
       if (tid == 0) {
         __threadfence();
         const unsigned int prev = atomicAdd(R.done, 1u);
