@@ -98,6 +98,59 @@ __global__ void __launch_bounds__(256) prep_kernel(const MatchLaunch L, const Ba
   const float inv_k = 1.0f / static_cast<float>(L.ref_count);
   float* mp = BW.mp + s * N * N;
   float* rp = BW.rp + s * N * N;
+  if constexpr (sizeof(TIn) == 1) {
+    // uint8: thread (row, group) takes PT consecutive pixels of one row.  The
+    // reference rows come in aligned 32-bit words (funnel-shifted to the
+    // window's byte offset; the word after the last needed byte is not read)
+    // and are summed over the sections as 16-bit integer lanes: exact, so
+    // the mean equals the float sum of the pixels in any order.
+    constexpr int PT = RB * N / 256;  // pixels per thread: n / 16
+    constexpr int NW = PT / 4;        // output words of four pixels
+    static_assert(PT % 4 == 0 && N / PT == 16, "16 threads per row, whole words");
+    const int i = rb * RB + tid / 16, x0 = (tid % 16) * PT;
+    uint32_t lo[NW], hi[NW];  // pixel sums: (p0, p1) and (p2, p3) of each word as 16-bit lanes
+#pragma unroll
+    for (int q = 0; q < NW; ++q) lo[q] = hi[q] = 0u;
+    for (int k = 0; k < L.ref_count; ++k) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(ref + k * L.ref_stride + static_cast<long long>(i) * L.ref_pitch + x0);
+      const uint32_t* wp = reinterpret_cast<const uint32_t*>(a & ~static_cast<uintptr_t>(3));
+      const uint32_t sh = 8u * static_cast<uint32_t>(a & 3);
+      uint32_t w[NW + 1];
+#pragma unroll
+      for (int q = 0; q < NW; ++q) w[q] = __ldg(wp + q);
+      w[NW] = sh ? __ldg(wp + NW) : 0u;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        const uint32_t o = __funnelshift_r(w[q], w[q + 1], sh);
+        lo[q] += __byte_perm(o, 0u, 0x4140);
+        hi[q] += __byte_perm(o, 0u, 0x4342);
+      }
+    }
+    const float di = i - c;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      float4 r4 = make_float4(static_cast<float>(lo[q] & 0xffffu), static_cast<float>(lo[q] >> 16),
+                              static_cast<float>(hi[q] & 0xffffu), static_cast<float>(hi[q] >> 16));
+      if (L.ref_count > 1) r4 = make_float4(r4.x * inv_k, r4.y * inv_k, r4.z * inv_k, r4.w * inv_k);
+      *reinterpret_cast<float4*>(rp + i * N + x0 + 4 * q) = r4;
+      float mv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = x0 + 4 * q + u;
+        const float dj = j - c;
+        int y0, x0t;
+        float fy, fx;
+        warp_tap(cy, th[0] * di + th[1] * dj + th[2], L.mov_h - 2, y0, fy);
+        warp_tap(cx, th[3] * di + th[4] * dj + th[5], L.mov_w - 2, x0t, fx);
+        const TIn* p = mov + static_cast<long long>(y0) * L.mov_pitch + x0t;
+        const float s00 = load_px<TIn>(p), s01 = load_px<TIn>(p + 1);
+        const float s10 = load_px<TIn>(p + L.mov_pitch), s11 = load_px<TIn>(p + L.mov_pitch + 1);
+        mv[u] = (1.f - fy) * ((1.f - fx) * s00 + fx * s01) + fy * ((1.f - fx) * s10 + fx * s11);
+      }
+      *reinterpret_cast<float4*>(mp + i * N + x0 + 4 * q) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+    }
+    return;
+  }
   for (int e = tid; e < RB * N; e += 256) {
     const int i = rb * RB + e / N, j = e % N;
     // reference (mean of ref_count sections)
