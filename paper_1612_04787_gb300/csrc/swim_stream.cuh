@@ -420,6 +420,18 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
   TIn* mstage = reinterpret_cast<TIn*>(tapT + R2 * TS);  // [RB][MS]
   TIn* rstage = mstage + RB * MS;
   float* rfstage = reinterpret_cast<float*>(slab);
+  // the plan's tables are requested first (into registers, stored below)
+  constexpr int NT = (N + T - 1) / T;
+  float2 twr[NT];
+  float tpr[NT];
+#pragma unroll
+  for (int q = 0; q < NT; ++q) {
+    const int i = tid + q * T;
+    if (N % T == 0 || i < N) {
+      twr[q] = L.twiddle[i];
+      tpr[q] = L.taper[i];
+    }
+  }
   const TIn* mbase;
   const TIn* rbase;
   long long mpitch, rpitch;
@@ -440,8 +452,8 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
   }
   // uint8 section rows through the tensor maps (RowMaps): the tiles start at
   // the staging area's first 128-byte boundary (rows_smem leaves the slack);
-  // one thread issues both box copies before the tables are staged, so the
-  // copies run under the table loads
+  // one thread issues both box copies before the tables are stored, so the
+  // copies run under the table stores
   __shared__ __align__(8) unsigned long long stage_bar;
   const uint32_t mbar = smem_addr(&stage_bar);
   bool tma = false;
@@ -463,11 +475,14 @@ __device__ __forceinline__ void rows_stage(const MatchLaunch& L, const WinRef& R
       tma_load_3d(smem_addr(rtile), &M->ref, 0, rx >> 4, ry + rb * RB, mbar);
     }
   }
-  for (int i = tid; i < N; i += T) {
-    twid[i] = L.twiddle[i];
-    const float t = L.taper[i];
-    tap[i] = t;
-    tapT[(i % R2) * TS + i / R2] = t;
+#pragma unroll
+  for (int q = 0; q < NT; ++q) {
+    const int i = tid + q * T;
+    if (N % T == 0 || i < N) {
+      twid[i] = twr[q];
+      tap[i] = tpr[q];
+      tapT[(i % R2) * TS + i / R2] = tpr[q];
+    }
   }
   // a staging copy that did not arrive (bounded wait): the window is marked
   // SWIFT_WIN_TIMEOUT after one more wait for the copies in flight
