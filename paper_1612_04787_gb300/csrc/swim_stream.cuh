@@ -1181,10 +1181,8 @@ __device__ __forceinline__ void cpair_stage(const MatchLaunch& L, const WinRef& 
   }
 }
 
-// 3 CTAs per SM up to 128 x 128 (80 registers, no spills); 2 at 256 x 256,
-// whose pass-B registers spill under the 3-CTA cap (measured 15 % slower)
 template <int N, bool CORRECT = false>
-__global__ void __launch_bounds__(256, N <= 128 ? 3 : 2) stream_cpair_kernel(const MatchLaunch L, const StreamWork W) {
+__global__ void __launch_bounds__(256, 2) stream_cpair_kernel(const MatchLaunch L, const StreamWork W) {
   cpair_stage<N, CORRECT>(L, slice_ref<N>(L, W, blockIdx.x / PairGeom<N>::NB), blockIdx.x % PairGeom<N>::NB);
 }
 
